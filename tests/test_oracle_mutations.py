@@ -1,0 +1,78 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a private copy of the oracle's C source (never
+in the committed file), builds it on the CPU, and checks that at least one pin
+of ``test_oracle_pins`` fails against the mutated build.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle as orc
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(orc.__file__), "mbp_oracle.c")
+
+
+def _tree_pin():
+    for u in (1, 2, 3):
+        for trial in range(4):
+            pins.test_tree_codes_reach_exact_map(u, trial)
+
+
+def _parity_pin():
+    for d in (2, 3, 4):
+        for z in (0, 1):
+            pins.test_check_node_is_parity_posterior(d, z)
+
+
+def _frames_pin():
+    pins.test_small_code_converged_frames_are_the_unique_solution()
+
+
+def _syndrome_pin():
+    pins.test_syndrome_against_dense_gf2_and_linearity()
+
+
+def _llr_pin():
+    for e in (0.02, 0.1):
+        pins.test_bsc_llr_is_channel_likelihood_ratio(e)
+
+
+MUTATIONS = {
+    # variable-to-check message forgets the channel prior
+    "v2c_drops_prior": ("          double s = LP[i];\n          for (int64_t b", "          double s = 0.0;\n          for (int64_t b", _tree_pin),
+    # variable-to-check message keeps its own check's message (not extrinsic)
+    "v2c_not_extrinsic": ("if (b != a) s += c2v[C->col_edge[b]];", "s += c2v[C->col_edge[b]];", _tree_pin),
+    # syndrome sign of eq. (6) ignored
+    "c2v_ignores_syndrome": ("double s = z ? -1.0 : 1.0;\n  for (int k = 0; k < d; ++k) {\n    double ext;",
+                             "double s = 1.0;\n  for (int k = 0; k < d; ++k) {\n    double ext;", _tree_pin),
+    # wrong sign of the correction term of the boxplus
+    "boxplus_sign": ("- log1p(exp(-fabs(a - b)))", "+ log1p(exp(-fabs(a - b)))", _parity_pin),
+    # prefix combination shifted by one edge
+    "prefix_off_by_one": ("orc_boxplus(pre[k - 1], v2c[k - 1])", "orc_boxplus(pre[k - 1], v2c[k])", _parity_pin),
+    # posterior of eq. (2) forgets the channel prior
+    "posterior_drops_prior": ("        double s = LP[i];\n        for (int64_t a", "        double s = 0.0;\n        for (int64_t a", _tree_pin),
+    # hard decision with the wrong orientation
+    "hard_decision_flipped": ("set_bit(xhat, i, LV[i] < 0.0);", "set_bit(xhat, i, LV[i] > 0.0);", _frames_pin),
+    # syndrome of eq. (1) reads the wrong bit of x
+    "syndrome_wrong_bit": ("p ^= bit_of(x, C->edge_col[k]);", "p ^= bit_of(x, C->edge_col[k] + 1);", _syndrome_pin),
+    # eq. (5) with P^0 and P^1 swapped
+    "llr_orientation": ("L_P[i] = log(p0 / p1);", "L_P[i] = log(p1 / p0);", _llr_pin),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_mutation_is_caught(name, tmp_path):
+    old, new, pin = MUTATIONS[name]
+    src = open(SRC).read()
+    assert old in src, f"mutation anchor for {name} not found"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-shared", "-fPIC",
+                           "-o", str(so), str(mutated), "-lm", "-lpthread"])
+    with orc.library_override(str(so)):
+        with pytest.raises((AssertionError, RuntimeError, ValueError, ZeroDivisionError, FloatingPointError)):
+            pin()
