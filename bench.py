@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of batched multi-matrix BP reconciliation on GB300.
+
+One step = one mbp_decode_bsc call that reconciles a batch of BSC frames:
+n = 65536 bits per frame, u = 2 PEG matrices of rate 0.7 (m = 19661 each),
+variable degrees {2: 30%, 3: 40%, 8: 30%}, QBER 2%, 1024 frames, at most 60
+flooding iterations, FP32 messages. Frames are synthetic (seeded), the codes
+are built by the seeded PEG generator.
+
+The metric is corrected sifted key per second: sum over frames of n divided by
+the decode time, all frames counted (the frame error rate is reported beside
+it). ``value`` is timed with CUDA events on the decode stream with every input
+already in HBM; ``e2e`` times the host-memory entry point, which copies Bob's
+bits, the QBERs and Alice's syndromes in and the corrected bits, iteration
+counts and success flags out. The per-step decoder state (about 2.8 GB) is far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import mbp_inputs as mi  # noqa: E402
+
+N, M, DIST, U, SEED = 65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1
+QBER, MAX_ITER, FRAMES = 0.02, 60, 1024
+WORKLOAD = "MBP decode, n=65536, R=0.7 (m=19661 x u=2 PEG), dv {2:.3,3:.4,8:.3}, BSC QBER 2%, 1024 frames, max 60 it"
+METRIC = "corrected-key Mbps per GB300 at FER<=1e-3 (and % of HBM roofline) vs plain FP32 MBP"
+L_MAX = 20.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--frames", type=int, default=FRAMES)
+    p.add_argument("--cpu-sample", type=int, default=256, help="frames in the oracle's timed sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n, e_tot, msg_bytes=4):
+    """Per frame-iteration: the check kernel's floor (messages read + written once, posterior read once)
+    and the whole iteration's floor 2 s E + 12 n (posterior read, written and gathered once)."""
+    return 2 * msg_bytes * e_tot + 4 * n, 2 * msg_bytes * e_tot + 12 * n
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def cpu_count():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_time(H, x, y, e, frames, threads):
+    import oracle as orc
+    z = orc.syndrome(H, x[:frames])
+    LP = orc.bsc_llr(y[:frames], N, e[:frames])
+    t0 = time.perf_counter()
+    out = orc.decode(H, LP, z, MAX_ITER, l_max=L_MAX, threads=threads)
+    dt = time.perf_counter() - t0
+    return dt, out
+
+
+def kernel_traffic(mean_frames_per_launch):
+    """DRAM bytes per check-kernel launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "check_node_kernel_n65536.txt")
+    src = os.path.join(ROOT, "paper_2001_07979_gb300", "csrc", "mbp_kernels.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = dict(line.split("=", 1) for line in text.splitlines() if "=" in line and not line.startswith("#"))
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if kv.get("kernel_source_sha256_16") != digest:
+            return None
+        return float(kv["dram_bytes_per_frame_iteration"]) * mean_frames_per_launch
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    H = mi.make_codes(N, M, DIST, U, SEED)
+    sample = 32
+    x, y, e = mi.bsc_frames(N, sample, QBER, seed=SEED)
+    threads = cpu_count()
+    for _ in range(args.warmup):
+        oracle_time(H, x, y, e, sample, threads)
+    times, fails = [], 0
+    for _ in range(args.steps):
+        dt, out = oracle_time(H, x, y, e, sample, threads)
+        times.append(dt)
+        fails = int((out["success"] == 0).sum())
+    ms = 1e3 * sum(times) / len(times)
+    value = sample * N / (ms / 1e3) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mbps", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": sample, "fer": fails / sample},
+        "cpu_baseline": {"value": value, "unit": "Mbps", "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} frames of the workload per step, FP64 oracle, {threads} threads"},
+        "e2e": {"value": value, "unit": "Mbps", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2001_07979_gb300 as mbp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        mbp.build()
+    if world > 1:
+        dist.barrier()
+    mbp._load()
+
+    F = args.frames
+    H = mi.make_codes(N, M, DIST, U, SEED)
+    x, y, e = mi.bsc_frames(N, F, QBER, seed=SEED, stream=rank)
+    codes = mbp.mbp_create_codes(H)
+    dev = torch.device("cuda", local)
+    xd = torch.from_numpy(x.view(np.int32)).to(dev)
+    yd = torch.from_numpy(y.view(np.int32)).to(dev)
+    ed = torch.from_numpy(e).to(dev)
+    zd = mbp.mbp_syndrome(codes, xd)  # Alice's side, untimed
+    ws = torch.empty(mbp.mbp_decode_workspace_size(codes, F, mbp.MSG_F32), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=mbp.MSG_F32, l_max=L_MAX, workspace=ws)
+
+    for _ in range(max(args.warmup, 3)):
+        out = step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mbp.mbp_profile_enable(True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = mbp.mbp_profile_get()
+    mbp.mbp_profile_enable(False)
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+
+    iters = out["iters"].cpu().numpy()
+    ok = out["success"].cpu().numpy().astype(bool)
+    xh = out["x_hat_bits"].cpu().numpy().view(np.uint32)
+    fails = int((~ok).sum())
+    undetected = int(np.sum(ok & ~np.all(xh == x, axis=1)))
+
+    # end-to-end through the host-memory entry point: copies in and out inside the timed region
+    Wn = (N + 31) // 32
+    yh = torch.from_numpy(y.view(np.int32)).pin_memory()
+    eh = torch.from_numpy(e).pin_memory()
+    zh = zd.cpu().pin_memory()
+    outh = dict(x_hat_bits=torch.empty((F, Wn), dtype=torch.int32).pin_memory(),
+                iters=torch.empty(F, dtype=torch.int32).pin_memory(),
+                success=torch.empty(F, dtype=torch.uint8).pin_memory())
+    wsh = torch.empty(mbp.mbp_decode_workspace_size(codes, F, mbp.MSG_F32, host_io=True), dtype=torch.uint8,
+                      device=dev)
+
+    def step_e2e():
+        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, l_max=L_MAX, workspace=wsh, out=outh)
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    assert np.array_equal(outh["x_hat_bits"].numpy().view(np.uint32), xh)
+    h2d = yh.numel() * 4 + eh.numel() * 8 + zh.numel() * 4
+    d2h = outh["x_hat_bits"].numel() * 4 + F * 4 + F
+
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+        fails_t = torch.tensor([fails, undetected], dtype=torch.int64, device=dev)
+        dist.all_reduce(fails_t)
+        fails, undetected = int(fails_t[0]), int(fails_t[1])
+
+    bits = F * N * world
+    value = bits / (ms / 1e3) / 1e6
+    value_e2e = bits / (ms_e2e / 1e3) / 1e6
+
+    # roofline of the dominant kernel: algorithmic bytes of the frame-iterations it ran / its event time
+    e_tot = codes.edges
+    b_check, b_iter = algorithmic_bytes(N, e_tot)
+    frame_iters = int(iters.sum()) * args.steps
+    n_check, ms_check = prof["check"]
+    peak, peak_src = load_peaks()
+    achieved = b_check * frame_iters / (ms_check / 1e3) / 1e9 if ms_check > 0 else None
+    mean_frames = frame_iters / n_check if n_check else 0
+    traffic = kernel_traffic(mean_frames)
+    dominant = max(prof, key=lambda k: prof[k][1])
+    launches = int(sum(v[0] for v in prof.values()))
+    path_gbs = b_iter * frame_iters / (ms * args.steps / 1e3) / 1e9
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": "Mbps", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_gpu": F, "n": N, "m_per_matrix": M, "u": U,
+                       "edges": e_tot, "qber": QBER, "max_iter": MAX_ITER, "l_max": L_MAX,
+                       "mean_iterations": float(iters.mean()), "max_iterations": int(iters.max()),
+                       "fer": fails / (F * world), "undetected_errors": undetected,
+                       "l2": "per-step decoder state ~2.8 GB > 129 MB L2 (no flush)",
+                       "parallelism": f"replicas x{world} (frames sharded, no collective on the path)"},
+            "roofline": {"bound": "hbm", "kernel": "cn_kernel (check-node update, eq. 6)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "peak_source": f"{peak_src} HBM copy bandwidth",
+                         "bytes_per_frame_iteration": b_check, "launches": n_check,
+                         "mean_launch_ms": ms_check / n_check if n_check else None,
+                         "dominant_family": dominant,
+                         "path_gbs_at_2sE_plus_12n": path_gbs, "path_frac": path_gbs / peak},
+            "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": value_e2e, "unit": "Mbps", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": ms_e2e},
+            "context": "paper: 85.67 Mbps average / 102.084 Mbps maximum on TitanV (other codes, other hardware)",
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            threads = cpu_count()
+            sample = min(args.cpu_sample, F)
+            dt, ref = oracle_time(H, x, y, e, sample, threads)
+            agree = bool(np.array_equal(ref["x_hat_bits"], xh[:sample]))
+            result["cpu_baseline"] = {"value": sample * N / dt / 1e6, "unit": "Mbps", "cores": threads,
+                                      "kind": "oracle",
+                                      "sample": f"first {sample} of the {F} frames, FP64 oracle, {dt:.1f} s",
+                                      "outputs_agree": agree}
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,338 @@
+"""GB300 multi-matrix belief-propagation (MBP) reconciliation — Python binding.
+
+A thin ctypes layer over ``libmbp.so`` (the C ABI in ``include/mbp.h``). It
+marshals arguments only: every step of decoding runs in the library's CUDA
+kernels. PyTorch provides device memory and streams. There is no CPU fallback:
+if the library is not built, every entry point raises.
+
+Function names follow the C ABI (``mbp_create_codes``, ``mbp_syndrome``,
+``mbp_bsc_llr``, ``mbp_decode_batch``, ``mbp_decode_bsc``,
+``mbp_decode_bsc_host``, ``mbp_export_c2v``, ...). Bit vectors are int32
+tensors holding the packed uint32 words of the ABI (bit i of a frame in word
+i >> 5 at position i & 31).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from ._build import LIB, build, up_to_date
+
+__all__ = [
+    "build", "library_path", "MBPError", "Codes", "MSG_F32", "MSG_F64",
+    "mbp_create_codes", "mbp_destroy_codes", "mbp_syndrome", "mbp_bsc_llr", "mbp_decode_workspace_size",
+    "mbp_decode_batch", "mbp_decode_bsc", "mbp_decode_bsc_host", "mbp_export_c2v", "mbp_version",
+    "split_syndromes", "join_syndromes", "mbp_profile_enable", "mbp_profile_get", "KERNEL_FAMILIES",
+]
+
+MSG_F32, MSG_F64 = 0, 1
+_STATUS = {0: "MBP_OK", 1: "MBP_EINVAL", 2: "MBP_ENOMEM", 3: "MBP_ECUDA", 4: "MBP_ETIMEOUT", 5: "MBP_EUNSUPPORTED"}
+
+
+class MBPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("msg_dtype", ctypes.c_int32), ("early_exit", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("host_io", ctypes.c_int32), ("l_max", ctypes.c_double), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("soft_out", ctypes.c_void_p), ("synd_ok", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB):
+            raise MBPError(3, f"{LIB} is not built; call paper_2001_07979_gb300.build() (needs nvcc)")
+        lib = ctypes.CDLL(LIB)
+        P, I, I64, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        sig = {
+            "mbp_last_error_string": (ctypes.c_char_p, []),
+            "mbp_version": (I, []),
+            "mbp_default_opts": (None, [P]),
+            "mbp_create_codes": (I, [P, I, P]),
+            "mbp_destroy_codes": (I, [P]),
+            "mbp_codes_info": (I, [P, P, P, P, P, P]),
+            "mbp_syndrome": (I, [P, P, I, P, P]),
+            "mbp_bsc_llr": (I, [P, P, I, I, I, P, P]),
+            "mbp_decode_workspace_size": (I, [P, I, P, P]),
+            "mbp_decode_batch": (I, [P, I, P, P, I, P, P, P, P, P]),
+            "mbp_decode_bsc": (I, [P, I, P, P, P, I, P, P, P, P, P]),
+            "mbp_decode_bsc_host": (I, [P, I, P, P, P, I, P, P, P, P, P]),
+            "mbp_export_c2v": (I, [P, I, P, I, P, P]),
+            "mbp_profile_enable": (I, [I]),
+            "mbp_profile_get": (I, [I, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        del I64, S
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = _load().mbp_last_error_string().decode(errors="replace")
+        raise MBPError(rc, msg)
+
+
+def mbp_version() -> int:
+    return _load().mbp_version()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+def _words(nbits: int) -> int:
+    return (nbits + 31) // 32
+
+
+class Codes:
+    """Handle of u matrices uploaded with ``mbp_create_codes``."""
+
+    def __init__(self, handle: int, n: int, m: list[int], edges: int, max_deg: int):
+        self._h = handle
+        self.n, self.m, self.u, self.edges, self.max_check_degree = n, m, len(m), edges, max_deg
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise MBPError(1, "codes handle was destroyed")
+        return self._h
+
+    def syndrome_words(self) -> list[int]:
+        return [_words(ml) for ml in self.m]
+
+    def destroy(self):
+        if self._h:
+            h, self._h = self._h, None
+            _check(_load().mbp_destroy_codes(h))
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.mbp_destroy_codes(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def mbp_create_codes(matrices) -> Codes:
+    """Upload u CSR matrices (objects with n, m, row_ptr, col_idx) to the current device."""
+    lib = _load()
+    u = len(matrices)
+    keep, arr = [], (_Csr * max(u, 1))()
+    for l, h in enumerate(matrices):
+        rp = np.ascontiguousarray(h.row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(h.col_idx, dtype=np.int32)
+        keep += [rp, ci]
+        arr[l] = _Csr(int(h.n), int(h.m), int(rp[-1]) if rp.size else 0, rp.ctypes.data,
+                      ci.ctypes.data if ci.size else None)
+    out = ctypes.c_void_p()
+    _check(lib.mbp_create_codes(ctypes.addressof(arr), u, ctypes.byref(out)))
+    n = ctypes.c_int32()
+    e = ctypes.c_int64()
+    d = ctypes.c_int32()
+    _check(lib.mbp_codes_info(out, None, ctypes.byref(n), None, ctypes.byref(e), ctypes.byref(d)))
+    return Codes(out.value, n.value, [int(h.m) for h in matrices], e.value, d.value)
+
+
+def mbp_destroy_codes(codes: Codes):
+    codes.destroy()
+
+
+def mbp_syndrome(codes: Codes, x_bits: torch.Tensor, stream=None) -> torch.Tensor:
+    """eq. (1) on the device: x_bits int32 [F, ceil(n/32)] -> z int32 [sum_l F*ceil(m_l/32)] ([u][F][W_l])."""
+    x = x_bits.contiguous()
+    F = x.shape[0]
+    z = torch.empty(F * sum(codes.syndrome_words()), dtype=torch.int32, device=x.device)
+    _check(_load().mbp_syndrome(codes.handle, _ptr(x), F, _ptr(z), _stream_ptr(stream)))
+    return z
+
+
+def split_syndromes(codes: Codes, z_flat, F: int):
+    """Flat [u][F][W_l] syndromes -> list of u arrays/tensors [F, W_l]."""
+    out, off = [], 0
+    for w in codes.syndrome_words():
+        out.append(z_flat[off:off + F * w].reshape(F, w))
+        off += F * w
+    return out
+
+
+def join_syndromes(parts):
+    if isinstance(parts[0], torch.Tensor):
+        return torch.cat([p.reshape(-1) for p in parts]).contiguous()
+    return np.ascontiguousarray(np.concatenate([np.asarray(p).reshape(-1) for p in parts]))
+
+
+def mbp_bsc_llr(y_bits: torch.Tensor, qber: torch.Tensor, n: int, dtype=torch.float32, stream=None) -> torch.Tensor:
+    """eq. (5) on the device: y_bits int32 [F, W], qber float64 [F] -> LLR [F, n]."""
+    y = y_bits.contiguous()
+    q = qber.to(torch.float64).contiguous()
+    F = y.shape[0]
+    code = MSG_F64 if dtype == torch.float64 else MSG_F32
+    out = torch.empty((F, n), dtype=torch.float64 if code == MSG_F64 else torch.float32, device=y.device)
+    _check(_load().mbp_bsc_llr(_ptr(y), _ptr(q), F, n, code, _ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def _opts(msg_dtype, l_max, early_exit, validate, host_io, workspace=None, soft=None, synd=None) -> _Opts:
+    o = _Opts()
+    _load().mbp_default_opts(ctypes.byref(o))
+    o.msg_dtype = msg_dtype
+    o.l_max = float(l_max)
+    o.early_exit = int(bool(early_exit))
+    o.validate = int(bool(validate))
+    o.host_io = int(bool(host_io))
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel()
+    o.soft_out = _ptr(soft)
+    o.synd_ok = _ptr(synd)
+    return o
+
+
+def mbp_decode_workspace_size(codes: Codes, F: int, msg_dtype: int = MSG_F32, host_io: bool = False) -> int:
+    o = _opts(msg_dtype, 20.0, True, False, host_io)
+    b = ctypes.c_size_t()
+    _check(_load().mbp_decode_workspace_size(codes.handle, F, ctypes.byref(o), ctypes.byref(b)))
+    return b.value
+
+
+def _workspace(codes, F, msg_dtype, host_io, workspace, device):
+    need = mbp_decode_workspace_size(codes, F, msg_dtype, host_io)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+    return workspace
+
+
+def _decode(entry, codes, F, inputs, z_bits, max_iter, msg_dtype, l_max, early_exit, validate, want_soft,
+            want_synd, workspace, device, stream):
+    workspace = _workspace(codes, F, msg_dtype, False, workspace, device)
+    fdt = torch.float64 if msg_dtype == MSG_F64 else torch.float32
+    xh = torch.empty((F, _words(codes.n)), dtype=torch.int32, device=device)
+    it = torch.empty(F, dtype=torch.int32, device=device)
+    ok = torch.empty(F, dtype=torch.uint8, device=device)
+    soft = torch.empty((F, codes.n), dtype=fdt, device=device) if want_soft else None
+    synd = torch.empty((F, codes.u), dtype=torch.uint8, device=device) if want_synd else None
+    o = _opts(msg_dtype, l_max, early_exit, validate, False, workspace, soft, synd)
+    z = z_bits.contiguous()
+    _check(entry(codes.handle, F, *[_ptr(t) for t in inputs], _ptr(z), int(max_iter), ctypes.byref(o),
+                 _ptr(xh), _ptr(it), _ptr(ok), _stream_ptr(stream)))
+    out = dict(x_hat_bits=xh, iters=it, success=ok, workspace=workspace)
+    if want_soft:
+        out["soft"] = soft
+    if want_synd:
+        out["synd_ok"] = synd
+    return out
+
+
+def mbp_decode_batch(codes: Codes, llr: torch.Tensor, z_bits: torch.Tensor, max_iter: int, *, l_max: float = 20.0,
+                     early_exit: bool = True, validate: bool = False, want_soft: bool = False,
+                     want_synd: bool = False, workspace: torch.Tensor | None = None, stream=None) -> dict:
+    """Decode F frames from channel LLRs (float32 -> FP32 messages, float64 -> FP64 messages)."""
+    x = llr.contiguous()
+    msg = MSG_F64 if x.dtype == torch.float64 else MSG_F32
+    if x.dtype not in (torch.float32, torch.float64):
+        raise TypeError("llr must be float32 or float64")
+    return _decode(_load().mbp_decode_batch, codes, x.shape[0], [x], z_bits, max_iter, msg, l_max, early_exit,
+                   validate, want_soft, want_synd, workspace, x.device, stream)
+
+
+def mbp_decode_bsc(codes: Codes, y_bits: torch.Tensor, qber: torch.Tensor, z_bits: torch.Tensor, max_iter: int, *,
+                   msg_dtype: int = MSG_F32, l_max: float = 20.0, early_exit: bool = True, want_soft: bool = False,
+                   want_synd: bool = False, workspace: torch.Tensor | None = None, stream=None) -> dict:
+    """Decode F BSC frames from Bob's bits and per-frame QBER (eq. 5 formed on the device)."""
+    y = y_bits.contiguous()
+    q = qber.to(torch.float64).contiguous()
+    return _decode(_load().mbp_decode_bsc, codes, y.shape[0], [y, q], z_bits, max_iter, msg_dtype, l_max,
+                   early_exit, False, want_soft, want_synd, workspace, y.device, stream)
+
+
+def mbp_decode_bsc_host(codes: Codes, y_bits: np.ndarray, qber: np.ndarray, z_bits: np.ndarray, max_iter: int, *,
+                        msg_dtype: int = MSG_F32, l_max: float = 20.0, early_exit: bool = True,
+                        workspace: torch.Tensor | None = None, out: dict | None = None, stream=None,
+                        device=None) -> dict:
+    """Host-memory variant: inputs and outputs are numpy arrays (or pinned CPU tensors)."""
+    y = y_bits if isinstance(y_bits, torch.Tensor) else np.ascontiguousarray(y_bits, dtype=np.uint32)
+    q = qber if isinstance(qber, torch.Tensor) else np.ascontiguousarray(qber, dtype=np.float64)
+    z = z_bits if isinstance(z_bits, torch.Tensor) else np.ascontiguousarray(z_bits, dtype=np.uint32)
+    F = y.shape[0]
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    need = mbp_decode_workspace_size(codes, F, msg_dtype, True)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    if out is None:
+        out = dict(x_hat_bits=np.zeros((F, _words(codes.n)), np.uint32), iters=np.zeros(F, np.int32),
+                   success=np.zeros(F, np.uint8))
+    o = _opts(msg_dtype, l_max, early_exit, False, True, workspace)
+    _check(_load().mbp_decode_bsc_host(codes.handle, F, _ptr(y), _ptr(q), _ptr(z), int(max_iter), ctypes.byref(o),
+                                       _ptr(out["x_hat_bits"]), _ptr(out["iters"]), _ptr(out["success"]),
+                                       _stream_ptr(stream)))
+    out["workspace"] = workspace
+    return out
+
+
+def mbp_export_c2v(codes: Codes, F: int, workspace: torch.Tensor, frame: int, msg_dtype: int = MSG_F32,
+                   stream=None) -> torch.Tensor:
+    """Check-to-variable messages of one frame after a decode, in stacked CSR edge order."""
+    fdt = torch.float64 if msg_dtype == MSG_F64 else torch.float32
+    out = torch.empty(codes.edges, dtype=fdt, device=workspace.device)
+    o = _opts(msg_dtype, 20.0, True, False, False, workspace)
+    _check(_load().mbp_export_c2v(codes.handle, F, ctypes.byref(o), int(frame), _ptr(out), _stream_ptr(stream)))
+    return out
+
+
+KERNEL_FAMILIES = ("check", "variable", "syndrome", "retire", "setup", "output")
+
+
+def mbp_profile_enable(on: bool = True):
+    """Start (and clear) or stop per-kernel CUDA-event accounting of this thread's decode calls."""
+    _check(_load().mbp_profile_enable(int(bool(on))))
+
+
+def mbp_profile_get() -> dict:
+    """{family: (launches, milliseconds)} accumulated since mbp_profile_enable(True)."""
+    out = {}
+    for k, name in enumerate(KERNEL_FAMILIES):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(_load().mbp_profile_get(k, ctypes.byref(n), ctypes.byref(ms)))
+        out[name] = (n.value, ms.value)
+    return out

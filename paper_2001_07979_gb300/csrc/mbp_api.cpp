@@ -1,0 +1,496 @@
+// C ABI of libmbp: argument validation, code upload and the entry points
+// declared in include/mbp.h. Kernels and the decode driver are in mbp_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mbp_internal.h"
+
+namespace mbp {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  return set_error(MBP_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- kernel accounting (mbp_profile_*)
+namespace {
+struct Prof {
+  struct Pending {
+    int family, kernels;
+    cudaEvent_t a, b;
+  };
+  bool on = false;
+  int64_t launches[MBP_KERNEL_FAMILIES] = {};
+  double ms[MBP_KERNEL_FAMILIES] = {};
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open = nullptr;
+  cudaEvent_t take() {
+    if (pool.empty()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  void drain() {
+    for (auto& p : pending) {
+      float t = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        ms[p.family] += t;
+        launches[p.family] += p.kernels;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+};
+thread_local Prof g_prof;
+}  // namespace
+
+void prof_enable(bool on) {
+  g_prof.drain();
+  for (int k = 0; k < MBP_KERNEL_FAMILIES; ++k) {
+    g_prof.launches[k] = 0;
+    g_prof.ms[k] = 0.0;
+  }
+  g_prof.on = on;
+}
+
+bool prof_on() { return g_prof.on; }
+
+void prof_begin(int, cudaStream_t s) {
+  if (!g_prof.on) return;
+  g_prof.open = g_prof.take();
+  if (g_prof.open) cudaEventRecord(g_prof.open, s);
+}
+
+void prof_end(int family, cudaStream_t s, int kernels) {
+  if (!g_prof.on || !g_prof.open) return;
+  cudaEvent_t e = g_prof.take();
+  if (!e) return;
+  cudaEventRecord(e, s);
+  g_prof.pending.push_back({family, kernels, g_prof.open, e});
+  g_prof.open = nullptr;
+  if (g_prof.pending.size() > 512) g_prof.drain();
+}
+
+int prof_get(int family, int64_t* launches, double* ms) {
+  if (family < 0 || family >= MBP_KERNEL_FAMILIES) return set_error(MBP_EINVAL, "unknown kernel family %d", family);
+  g_prof.drain();
+  if (launches) *launches = g_prof.launches[family];
+  if (ms) *ms = g_prof.ms[family];
+  return MBP_OK;
+}
+
+}  // namespace mbp
+
+using namespace mbp;
+
+namespace {
+
+#define REQUIRE(cond, ...)                         \
+  do {                                             \
+    if (!(cond)) return set_error(MBP_EINVAL, __VA_ARGS__); \
+  } while (0)
+
+#define REQUIRE_DEV(p, name) \
+  REQUIRE(is_device_ptr(p), "%s must be a device pointer of the current device", name)
+
+int validate_opts(const mbp_opts* o) {
+  REQUIRE(o, "opts is NULL");
+  REQUIRE(o->msg_dtype == MBP_MSG_F32 || o->msg_dtype == MBP_MSG_F64, "unknown msg_dtype %d", o->msg_dtype);
+  REQUIRE(o->early_exit == 0 || o->early_exit == 1, "early_exit must be 0 or 1");
+  REQUIRE(std::isfinite(o->l_max) && o->l_max > 0, "l_max must be finite and > 0");
+  return MBP_OK;
+}
+
+int check_workspace(const mbp_codes* c, int F, const mbp_opts* o) {
+  size_t need = workspace_bytes(c->d, F, o->msg_dtype, o->host_io != 0);
+  REQUIRE(o->workspace, "opts->workspace is NULL (size it with mbp_decode_workspace_size)");
+  REQUIRE((reinterpret_cast<uintptr_t>(o->workspace) & 255) == 0, "workspace must be 256-byte aligned");
+  REQUIRE(o->workspace_bytes >= need, "workspace too small: %zu bytes given, %zu needed", o->workspace_bytes, need);
+  REQUIRE_DEV(o->workspace, "workspace");
+  return MBP_OK;
+}
+
+int common_decode_checks(const mbp_codes* codes, int F, int max_iter, const mbp_opts* opts) {
+  REQUIRE(codes, "codes is NULL");
+  REQUIRE(F >= 0, "F must be >= 0");
+  REQUIRE(max_iter >= 0 && max_iter <= 1000000, "max_iter must be in [0, 1e6]");
+  if (F == 0) return MBP_OK;
+  int rc = validate_opts(opts);
+  if (rc) return rc;
+  return check_workspace(codes, F, opts);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mbp_default_opts(mbp_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->msg_dtype = MBP_MSG_F32;
+  o->early_exit = 1;
+  o->l_max = 20.0;
+}
+
+const char* mbp_last_error_string(void) { return g_err.c_str(); }
+
+int mbp_version(void) { return 100; }
+
+int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
+  g_err.clear();
+  REQUIRE(out, "out is NULL");
+  *out = nullptr;
+  REQUIRE(H, "H is NULL");
+  REQUIRE(u >= 1, "u must be >= 1");
+  if (u > kMaxU) return set_error(MBP_EUNSUPPORTED, "u = %d exceeds the limit of %d matrices", u, kMaxU);
+  const int32_t n = H[0].n;
+  REQUIRE(n > 0, "n must be > 0");
+  int64_t m_tot = 0, e_tot = 0;
+  for (int l = 0; l < u; ++l) {
+    const mbp_csr& h = H[l];
+    REQUIRE(h.n == n, "matrix %d has n = %d, matrix 0 has n = %d", l, h.n, n);
+    REQUIRE(h.m >= 0 && h.nnz >= 0, "matrix %d: negative m or nnz", l);
+    REQUIRE(h.row_ptr, "matrix %d: row_ptr is NULL", l);
+    REQUIRE(h.nnz == 0 || h.col_idx, "matrix %d: col_idx is NULL", l);
+    REQUIRE(h.row_ptr[0] == 0, "matrix %d: row_ptr[0] != 0", l);
+    for (int32_t j = 0; j < h.m; ++j)
+      REQUIRE(h.row_ptr[j + 1] >= h.row_ptr[j], "matrix %d: row_ptr decreases at row %d", l, j);
+    REQUIRE(h.row_ptr[h.m] == h.nnz, "matrix %d: row_ptr[m] = %d != nnz = %d", l, h.row_ptr[h.m], h.nnz);
+    std::vector<int32_t> row;
+    for (int32_t j = 0; j < h.m; ++j) {
+      const int32_t d = h.row_ptr[j + 1] - h.row_ptr[j];
+      if (d > kMaxRowDeg)
+        return set_error(MBP_EUNSUPPORTED, "matrix %d row %d has %d edges; the limit is %d", l, j, d, kMaxRowDeg);
+      row.assign(h.col_idx + h.row_ptr[j], h.col_idx + h.row_ptr[j + 1]);
+      for (int32_t c : row) REQUIRE(c >= 0 && c < n, "matrix %d row %d: column %d outside [0, %d)", l, j, c, n);
+      std::sort(row.begin(), row.end());
+      REQUIRE(std::adjacent_find(row.begin(), row.end()) == row.end(), "matrix %d row %d repeats a column", l, j);
+    }
+    m_tot += h.m;
+    e_tot += h.nnz;
+  }
+  REQUIRE(m_tot <= INT32_MAX / 2 && e_tot <= INT32_MAX / 2, "code too large");
+
+  // ---- host layout
+  DevCode d{};
+  d.n = n;
+  d.u = u;
+  d.m_tot = static_cast<int32_t>(m_tot);
+  d.e_tot = e_tot;
+  d.row_first[0] = 0;
+  for (int l = 0; l < u; ++l) {
+    d.m[l] = H[l].m;
+    d.row_first[l + 1] = d.row_first[l] + H[l].m;
+  }
+  const int32_t n_slices = static_cast<int32_t>((m_tot + kSliceRows - 1) / kSliceRows);
+  d.n_slices = n_slices;
+  std::vector<int32_t> row_ptr(m_tot + 1), col_idx(std::max<int64_t>(e_tot, 1)), row_deg(m_tot);
+  std::vector<uint8_t> row_mat(std::max<int64_t>(m_tot, 1));
+  {
+    int64_t e = 0, r = 0;
+    row_ptr[0] = 0;
+    for (int l = 0; l < u; ++l)
+      for (int32_t j = 0; j < H[l].m; ++j, ++r) {
+        for (int32_t k = H[l].row_ptr[j]; k < H[l].row_ptr[j + 1]; ++k) col_idx[e++] = H[l].col_idx[k];
+        row_ptr[r + 1] = static_cast<int32_t>(e);
+        row_deg[r] = row_ptr[r + 1] - row_ptr[r];
+        row_mat[r] = static_cast<uint8_t>(l);
+      }
+  }
+  int32_t max_deg = 0;
+  for (int64_t r = 0; r < m_tot; ++r) max_deg = std::max(max_deg, row_deg[r]);
+  d.max_row_deg = max_deg;
+  std::vector<int32_t> slice_base(n_slices + 1);
+  slice_base[0] = 0;
+  for (int32_t s = 0; s < n_slices; ++s) {
+    int32_t dm = 0;
+    for (int q = 0; q < kSliceRows; ++q) {
+      int64_t r = int64_t(s) * kSliceRows + q;
+      if (r < m_tot) dm = std::max(dm, row_deg[r]);
+    }
+    int64_t next = int64_t(slice_base[s]) + int64_t(dm) * kSliceRows;
+    REQUIRE(next <= INT32_MAX / 2, "code too large");
+    slice_base[s + 1] = static_cast<int32_t>(next);
+  }
+  d.s_tot = slice_base[n_slices];
+  std::vector<int32_t> slot_col(std::max<int64_t>(d.s_tot, 1), -1), edge_slot(std::max<int64_t>(e_tot, 1));
+  for (int64_t r = 0; r < m_tot; ++r) {
+    int32_t s = static_cast<int32_t>(r / kSliceRows), q = static_cast<int32_t>(r % kSliceRows);
+    for (int32_t k = 0; k < row_deg[r]; ++k) {
+      int32_t slot = slice_base[s] + k * kSliceRows + q;
+      slot_col[slot] = col_idx[row_ptr[r] + k];
+      edge_slot[row_ptr[r] + k] = slot;
+    }
+  }
+  std::vector<int32_t> col_ptr(n + 1, 0), col_slot(std::max<int64_t>(e_tot, 1));
+  for (int64_t e = 0; e < e_tot; ++e) col_ptr[col_idx[e] + 1]++;
+  for (int32_t i = 0; i < n; ++i) col_ptr[i + 1] += col_ptr[i];
+  {
+    std::vector<int32_t> fill(col_ptr.begin(), col_ptr.end() - 1);
+    for (int64_t e = 0; e < e_tot; ++e) col_slot[fill[col_idx[e]]++] = edge_slot[e];  // stacked-row order
+  }
+
+  // ---- one device block for every array
+  struct Part { const void* src; size_t bytes; size_t off; };
+  std::vector<Part> parts = {
+      {slice_base.data(), slice_base.size() * 4, 0}, {slot_col.data(), slot_col.size() * 4, 0},
+      {col_ptr.data(), col_ptr.size() * 4, 0},       {col_slot.data(), col_slot.size() * 4, 0},
+      {row_ptr.data(), row_ptr.size() * 4, 0},       {col_idx.data(), col_idx.size() * 4, 0},
+      {edge_slot.data(), edge_slot.size() * 4, 0},   {row_mat.data(), row_mat.size(), 0}};
+  size_t total = 0;
+  for (auto& p : parts) {
+    p.off = total;
+    total += (p.bytes + 255) & ~size_t(255);
+  }
+  mbp_codes* h = new (std::nothrow) mbp_codes{};
+  if (!h) return set_error(MBP_ENOMEM, "host allocation failed");
+  cudaError_t ce = cudaGetDevice(&h->device);
+  if (ce != cudaSuccess) { delete h; return cuda_error(ce, "cudaGetDevice"); }
+  ce = cudaMalloc(&h->dev_block, total);
+  if (ce != cudaSuccess) {
+    delete h;
+    cudaGetLastError();
+    return set_error(MBP_ENOMEM, "cudaMalloc of %zu bytes for the code failed: %s", total, cudaGetErrorString(ce));
+  }
+  h->dev_bytes = total;
+  char* base = static_cast<char*>(h->dev_block);
+  for (auto& p : parts) {
+    ce = cudaMemcpy(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      cudaFree(h->dev_block);
+      delete h;
+      return cuda_error(ce, "cudaMemcpy of the code");
+    }
+  }
+  d.slice_base = reinterpret_cast<const int32_t*>(base + parts[0].off);
+  d.slot_col = reinterpret_cast<const int32_t*>(base + parts[1].off);
+  d.col_ptr = reinterpret_cast<const int32_t*>(base + parts[2].off);
+  d.col_slot = reinterpret_cast<const int32_t*>(base + parts[3].off);
+  d.row_ptr = reinterpret_cast<const int32_t*>(base + parts[4].off);
+  d.col_idx = reinterpret_cast<const int32_t*>(base + parts[5].off);
+  d.edge_slot = reinterpret_cast<const int32_t*>(base + parts[6].off);
+  d.row_mat = reinterpret_cast<const uint8_t*>(base + parts[7].off);
+  h->d = d;
+  *out = h;
+  return MBP_OK;
+}
+
+int mbp_destroy_codes(mbp_codes* codes) {
+  g_err.clear();
+  if (!codes) return MBP_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaError_t f = cudaFree(codes->dev_block);
+  delete codes;
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  if (f != cudaSuccess) return cuda_error(f, "cudaFree");
+  return MBP_OK;
+}
+
+int mbp_codes_info(const mbp_codes* c, int32_t* u, int32_t* n, int32_t* m_total, int64_t* edges,
+                   int32_t* max_check_degree) {
+  g_err.clear();
+  REQUIRE(c, "codes is NULL");
+  if (u) *u = c->d.u;
+  if (n) *n = c->d.n;
+  if (m_total) *m_total = c->d.m_tot;
+  if (edges) *edges = c->d.e_tot;
+  if (max_check_degree) *max_check_degree = c->d.max_row_deg;
+  return MBP_OK;
+}
+
+int mbp_syndrome(const mbp_codes* codes, const uint32_t* x_bits, int F, uint32_t* z_bits, mbp_stream_t stream) {
+  g_err.clear();
+  REQUIRE(codes, "codes is NULL");
+  REQUIRE(F >= 0, "F must be >= 0");
+  if (F == 0) return MBP_OK;
+  REQUIRE_DEV(x_bits, "x_bits");
+  REQUIRE_DEV(z_bits, "z_bits");
+  cudaError_t e = launch_syndrome(codes->d, x_bits, F, z_bits, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MBP_OK : cuda_error(e, "syndrome kernel");
+}
+
+int mbp_bsc_llr(const uint32_t* y_bits, const double* qber, int F, int n, int dtype, void* llr,
+                mbp_stream_t stream) {
+  g_err.clear();
+  REQUIRE(F >= 0 && n > 0, "F must be >= 0 and n > 0");
+  REQUIRE(dtype == MBP_MSG_F32 || dtype == MBP_MSG_F64, "unknown dtype %d", dtype);
+  if (F == 0) return MBP_OK;
+  REQUIRE_DEV(y_bits, "y_bits");
+  REQUIRE_DEV(qber, "qber");
+  REQUIRE_DEV(llr, "llr");
+  cudaError_t e = launch_bsc_llr(y_bits, qber, F, n, dtype, llr, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MBP_OK : cuda_error(e, "bsc_llr kernel");
+}
+
+int mbp_decode_workspace_size(const mbp_codes* codes, int F, const mbp_opts* opts, size_t* bytes) {
+  g_err.clear();
+  REQUIRE(codes && bytes, "codes and bytes must be non-NULL");
+  REQUIRE(F >= 0, "F must be >= 0");
+  int rc = validate_opts(opts);
+  if (rc) return rc;
+  *bytes = workspace_bytes(codes->d, F, opts->msg_dtype, opts->host_io != 0);
+  return MBP_OK;
+}
+
+static int decode_common(const mbp_codes* codes, int F, const void* llr, const uint32_t* y_bits,
+                         const double* qber, const uint32_t* z_bits, int max_iter, const mbp_opts* opts,
+                         uint32_t* x_hat_bits, int32_t* iters, uint8_t* success, mbp_stream_t stream) {
+  int rc = common_decode_checks(codes, F, max_iter, opts);
+  if (rc || F == 0) return rc;
+  if (llr) REQUIRE_DEV(llr, "llr");
+  if (y_bits) {
+    REQUIRE_DEV(y_bits, "y_bits");
+    REQUIRE_DEV(qber, "qber");
+  }
+  REQUIRE_DEV(z_bits, "z_bits");
+  REQUIRE_DEV(x_hat_bits, "x_hat_bits");
+  REQUIRE_DEV(iters, "iters");
+  REQUIRE_DEV(success, "success");
+  if (opts->soft_out) REQUIRE_DEV(opts->soft_out, "opts->soft_out");
+  if (opts->synd_ok) REQUIRE_DEV(opts->synd_ok, "opts->synd_ok");
+  DevState st;
+  carve_workspace(codes->d, F, opts->msg_dtype, opts->host_io != 0, opts->workspace, &st);
+  DecodeArgs a{};
+  a.llr = llr;
+  a.y_bits = y_bits;
+  a.qber = qber;
+  a.z_bits = z_bits;
+  a.max_iter = max_iter;
+  a.early_exit = opts->early_exit;
+  a.validate = opts->validate;
+  a.l_max = opts->l_max;
+  a.x_hat_bits = x_hat_bits;
+  a.iters = iters;
+  a.success = success;
+  a.soft_out = opts->soft_out;
+  a.synd_ok = opts->synd_ok;
+  return decode(codes->d, st, opts->msg_dtype, a, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mbp_decode_batch(const mbp_codes* codes, int F, const void* llr, const uint32_t* z_bits, int max_iter,
+                     const mbp_opts* opts, uint32_t* x_hat_bits, int32_t* iters, uint8_t* success,
+                     mbp_stream_t stream) {
+  g_err.clear();
+  if (F > 0) REQUIRE(llr, "llr is NULL");
+  return decode_common(codes, F, llr, nullptr, nullptr, z_bits, max_iter, opts, x_hat_bits, iters, success, stream);
+}
+
+int mbp_decode_bsc(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                   const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                   int32_t* iters, uint8_t* success, mbp_stream_t stream) {
+  g_err.clear();
+  if (F > 0) REQUIRE(y_bits && qber, "y_bits and qber must be non-NULL");
+  return decode_common(codes, F, nullptr, y_bits, qber, z_bits, max_iter, opts, x_hat_bits, iters, success,
+                       stream);
+}
+
+int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                        const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                        int32_t* iters, uint8_t* success, mbp_stream_t stream) {
+  g_err.clear();
+  int rc = common_decode_checks(codes, F, max_iter, opts);
+  if (rc || F == 0) return rc;
+  REQUIRE(opts->host_io == 1, "opts->host_io must be 1 for mbp_decode_bsc_host");
+  REQUIRE(y_bits && qber && z_bits && x_hat_bits && iters && success, "host buffers must be non-NULL");
+  REQUIRE(opts->soft_out == nullptr || is_device_ptr(opts->soft_out), "opts->soft_out must be a device pointer");
+  REQUIRE(opts->synd_ok == nullptr || is_device_ptr(opts->synd_ok), "opts->synd_ok must be a device pointer");
+  const DevCode& d = codes->d;
+  DevState st;
+  carve_workspace(d, F, opts->msg_dtype, true, opts->workspace, &st);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t wn = (size_t(d.n) + 31) / 32;
+  size_t zw = 0;
+  for (int l = 0; l < d.u; ++l) zw += (size_t(d.m[l]) + 31) / 32;
+  cudaError_t e;
+#define CK(call, what) \
+  if ((e = (call)) != cudaSuccess) return cuda_error(e, what)
+  CK(cudaMemcpyAsync(st.io_y, y_bits, size_t(F) * wn * 4, cudaMemcpyHostToDevice, s), "copy y_bits to device");
+  CK(cudaMemcpyAsync(st.io_qber, qber, size_t(F) * 8, cudaMemcpyHostToDevice, s), "copy qber to device");
+  CK(cudaMemcpyAsync(st.io_z, z_bits, size_t(F) * zw * 4, cudaMemcpyHostToDevice, s), "copy z_bits to device");
+  DecodeArgs a{};
+  a.y_bits = st.io_y;
+  a.qber = st.io_qber;
+  a.z_bits = st.io_z;
+  a.max_iter = max_iter;
+  a.early_exit = opts->early_exit;
+  a.validate = opts->validate;
+  a.l_max = opts->l_max;
+  a.x_hat_bits = st.io_xhat;
+  a.iters = st.io_iters;
+  a.success = st.io_success;
+  a.soft_out = opts->soft_out;
+  a.synd_ok = opts->synd_ok;
+  rc = decode(d, st, opts->msg_dtype, a, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(x_hat_bits, st.io_xhat, size_t(F) * wn * 4, cudaMemcpyDeviceToHost, s), "copy x_hat to host");
+  CK(cudaMemcpyAsync(iters, st.io_iters, size_t(F) * 4, cudaMemcpyDeviceToHost, s), "copy iters to host");
+  CK(cudaMemcpyAsync(success, st.io_success, size_t(F), cudaMemcpyDeviceToHost, s), "copy success to host");
+  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+#undef CK
+  return MBP_OK;
+}
+
+int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int frame, void* c2v_out,
+                   mbp_stream_t stream) {
+  g_err.clear();
+  REQUIRE(codes, "codes is NULL");
+  REQUIRE(F > 0 && frame >= 0 && frame < F, "frame %d outside [0, F = %d)", frame, F);
+  int rc = validate_opts(opts);
+  if (rc) return rc;
+  rc = check_workspace(codes, F, opts);
+  if (rc) return rc;
+  REQUIRE_DEV(c2v_out, "c2v_out");
+  DevState st;
+  carve_workspace(codes->d, F, opts->msg_dtype, opts->host_io != 0, opts->workspace, &st);
+  cudaError_t e = launch_export_c2v(codes->d, st, opts->msg_dtype, frame, c2v_out,
+                                    reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MBP_OK : cuda_error(e, "export kernel");
+}
+
+int mbp_profile_enable(int on) {
+  g_err.clear();
+  prof_enable(on != 0);
+  return MBP_OK;
+}
+
+int mbp_profile_get(int family, int64_t* launches, double* milliseconds) {
+  g_err.clear();
+  return prof_get(family, launches, milliseconds);
+}
+
+}  // extern "C"

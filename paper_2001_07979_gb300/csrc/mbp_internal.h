@@ -1,0 +1,117 @@
+// Internal declarations of libmbp (not part of the C ABI).
+//
+// Device layout of the stacked code [H_1; ...; H_u] (Section 2: u matrices of
+// size m_l x n sharing the n variable nodes):
+//   * stacked row r = row_first[l] + j is row j of H_l;
+//   * rows are grouped in slices of kSliceRows consecutive rows; a slice whose
+//     longest row has d edges owns kSliceRows * d edge "slots", slot
+//     slice_base[s] + k * kSliceRows + q holding edge k of row kSliceRows*s + q
+//     (slot_col = -1 where that row is shorter: padding);
+//   * every per-edge message array is indexed [tile][slot][lane]: kLanes frames
+//     ("lanes") are interleaved so that one edge of kLanes frames is one
+//     contiguous 32-byte (FP32) or 64-byte (FP64) vector;
+//   * col_ptr/col_slot list, for every variable node, the slots of its edges in
+//     stacked-row order (the order in which eq. (2) sums them).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "mbp.h"
+
+namespace mbp {
+
+constexpr int kLanes = 8;       // frames interleaved per tile
+constexpr int kSliceRows = 4;   // rows per slice: one warp = kSliceRows rows x kLanes frames
+constexpr int kMaxU = 16;
+constexpr int kMaxRowDeg = 64;
+
+struct DevCode {
+  int32_t n, u, m_tot, n_slices;
+  int32_t max_row_deg;
+  int64_t e_tot, s_tot;
+  int32_t m[kMaxU];
+  int32_t row_first[kMaxU + 1];
+  const int32_t* slice_base;  // [n_slices + 1]
+  const int32_t* slot_col;    // [s_tot]
+  const int32_t* col_ptr;     // [n + 1]
+  const int32_t* col_slot;    // [e_tot]
+  const int32_t* row_ptr;     // [m_tot + 1] stacked CSR
+  const int32_t* col_idx;     // [e_tot]
+  const int32_t* edge_slot;   // [e_tot] stacked CSR edge -> slot
+  const uint8_t* row_mat;     // [m_tot] matrix index of each stacked row
+};
+
+// Per-call decoder state carved out of the caller's workspace.
+struct DevState {
+  int32_t F, n_tiles;
+  void* c2v;          // [n_tiles][s_tot][kLanes] message type
+  void* lv;           // [n_tiles][n][kLanes] posterior L_V of eq. (2)
+  void* lp;           // [n_tiles][n][kLanes] channel LLR L_P
+  uint8_t* xh;        // [n_tiles][n] hard decisions, bit lane
+  uint8_t* zt;        // [n_tiles][m_tot] syndrome bits, bit lane
+  uint32_t* active;   // [n_tiles] lanes still decoding
+  uint32_t* fail;     // [n_tiles][u] lanes whose hard decision violates some check of H_l
+  double* llr_mag;    // [F] ln((1 - e)/e) for the BSC entry points
+  int32_t* counters;  // [4]: unfinished tiles, non-finite flag
+  // staging for mbp_decode_bsc_host
+  uint32_t* io_y;
+  double* io_qber;
+  uint32_t* io_z;
+  uint32_t* io_xhat;
+  int32_t* io_iters;
+  uint8_t* io_success;
+};
+
+}  // namespace mbp
+
+struct mbp_codes {
+  mbp::DevCode d;
+  void* dev_block;
+  size_t dev_bytes;
+  int device;
+};
+
+namespace mbp {
+
+// error reporting (thread-local message)
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+// launchers (mbp_kernels.cu)
+cudaError_t launch_syndrome(const DevCode& c, const uint32_t* x_bits, int F, uint32_t* z_bits, cudaStream_t s);
+cudaError_t launch_bsc_llr(const uint32_t* y_bits, const double* qber, int F, int n, int dtype, void* llr,
+                           cudaStream_t s);
+size_t workspace_bytes(const DevCode& c, int F, int msg_dtype, bool host_io);
+void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void* base, DevState* st);
+
+struct DecodeArgs {
+  const void* llr;         // [F][n] or NULL when y_bits is used
+  const uint32_t* y_bits;  // [F][W] (BSC entry)
+  const double* qber;      // [F]   (BSC entry)
+  const uint32_t* z_bits;
+  int max_iter;
+  int early_exit;
+  int validate;
+  double l_max;
+  uint32_t* x_hat_bits;
+  int32_t* iters;
+  uint8_t* success;
+  void* soft_out;
+  uint8_t* synd_ok;
+};
+
+int decode(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s);
+
+// kernel accounting (mbp_profile_*), per host thread
+void prof_enable(bool on);
+bool prof_on();
+void prof_begin(int family, cudaStream_t s);
+void prof_end(int family, cudaStream_t s, int kernels);
+int prof_get(int family, int64_t* launches, double* ms);
+cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtype, int frame, void* out,
+                              cudaStream_t s);
+
+}  // namespace mbp

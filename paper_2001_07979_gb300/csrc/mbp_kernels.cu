@@ -1,0 +1,554 @@
+// CUDA kernels and decode driver of libmbp (sm_103a).
+//
+// One decode iteration (Section 3A, Algorithm 1, flooding over all u matrices)
+// is three kernels over the frame tiles that still have unfinished frames:
+//   cn_kernel   eq. (6) for every check of every matrix, on V2C = clip(L_V - C2V)
+//   vn_kernel   eq. (2): L_V = L_P + sum of the node's C2V over all u matrices,
+//               and the hard decision
+//   syn_kernel  + update_kernel: the stopping rule H_l x_hat = z^l for every l
+// Frames are interleaved kLanes = 8 per tile, so every random access to a
+// variable node or an edge moves one contiguous vector of 8 frames.
+//
+// Check-node arithmetic. For a check with incoming V2C values v_k, eq. (6) gives
+//   |C2V_k| = 2 atanh( prod_{r != k} tanh(|v_r| / 2) ),
+//   sign(C2V_k) = (-1)^{z_j} prod_{r != k} sign(v_r).
+// With delta_r = 1 - tanh(|v_r| / 2) = 2 / (1 + e^{|v_r|}) the product becomes
+// 1 - D_k with D_k = (+)_{r != k} delta_r under a (+) b = a + b - a b (the
+// complement of a product), and 2 atanh(1 - D) = ln((2 - D) / D). Working with
+// delta keeps full relative precision for reliable messages (delta ~ 2e^{-|v|})
+// where tanh rounds to 1 in FP32. The exclusion r != k uses prefix and suffix
+// (+)-combinations, never a division. Per edge this is two MUFU operations in,
+// two out (exp + reciprocal, reciprocal + log).
+#include <cstdio>
+
+#include "mbp_internal.h"
+
+namespace mbp {
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+template <typename M>
+struct Arith;
+
+template <>
+struct Arith<float> {
+  // 1 - tanh(a/2) for a >= 0
+  static __device__ __forceinline__ float delta(float a) { return __fdividef(2.0f, 1.0f + __expf(a)); }
+  // complement product a (+) b = a + b - a b
+  static __device__ __forceinline__ float oplus(float p, float d) { return fmaf(d, 1.0f - p, p); }
+  // 2 atanh(1 - D) = ln((2 - D) / D), >= 0
+  static __device__ __forceinline__ float mag(float D) { return fmaxf(__logf(__fdividef(2.0f - D, D)), 0.0f); }
+};
+
+template <>
+struct Arith<double> {
+  static __device__ __forceinline__ double delta(double a) { return 2.0 / (1.0 + exp(a)); }
+  static __device__ __forceinline__ double oplus(double p, double d) { return fma(d, 1.0 - p, p); }
+  static __device__ __forceinline__ double mag(double D) { return fmax(log((2.0 - D) / D), 0.0); }
+};
+
+template <typename M>
+__device__ __forceinline__ M clampm(M v, M L) {
+  return v > L ? L : (v < -L ? -L : v);
+}
+
+// ------------------------------------------------------------- eq. (1)
+
+// One thread per (frame, 32-row word) of matrix l.
+__global__ void syndrome_kernel(const DevCode c, int l, const uint32_t* __restrict__ x, int F,
+                                uint32_t* __restrict__ z_l) {
+  const int wl = (c.m[l] + 31) >> 5;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(F) * wl) return;
+  const int f = int(idx / wl), w = int(idx % wl);
+  const int wn = (c.n + 31) >> 5;
+  const uint32_t* xf = x + int64_t(f) * wn;
+  uint32_t bits = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int j = w * 32 + b;
+    if (j >= c.m[l]) break;
+    const int r = c.row_first[l] + j;
+    uint32_t p = 0;
+    for (int e = c.row_ptr[r]; e < c.row_ptr[r + 1]; ++e) {
+      const int col = c.col_idx[e];
+      p ^= (__ldg(xf + (col >> 5)) >> (col & 31)) & 1u;
+    }
+    bits |= p << b;
+  }
+  z_l[int64_t(f) * wl + w] = bits;
+}
+
+// ------------------------------------------------------------- eq. (5)
+
+// L_P = (1 - 2y) ln((1 - e)/e); ln((1 - e)/e) once per block in double precision.
+template <typename M>
+__global__ void bsc_llr_kernel(const uint32_t* __restrict__ y, const double* __restrict__ qber, int n,
+                               M* __restrict__ llr) {
+  __shared__ double mag;
+  const int f = blockIdx.y;
+  if (threadIdx.x == 0) {
+    const double e = qber[f];
+    mag = log((1.0 - e) / e);
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int wn = (n + 31) >> 5;
+  const uint32_t bit = (y[int64_t(f) * wn + (i >> 5)] >> (i & 31)) & 1u;
+  llr[int64_t(f) * n + i] = M(bit ? -mag : mag);
+}
+
+__global__ void frame_mag_kernel(const double* __restrict__ qber, int F, double* __restrict__ mag) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < F) {
+    const double e = qber[f];
+    mag[f] = log((1.0 - e) / e);
+  }
+}
+
+// ------------------------------------------------------------- set-up
+
+// L_P into the interleaved layout and the hard decision of iteration 0.
+// Block: 32 columns x 8 lanes.
+template <typename M>
+__global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr, const uint32_t* __restrict__ y,
+                               const double* __restrict__ mag, M* __restrict__ lp, uint8_t* __restrict__ xh,
+                               int32_t* __restrict__ counters, int validate) {
+  const int tile = blockIdx.y;
+  const int lane = threadIdx.x & 7;
+  const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const int f = tile * kLanes + lane;
+  const bool ok = col < c.n;
+  M v = M(0);
+  if (ok && f < F) {
+    if (llr) {
+      v = llr[int64_t(f) * c.n + col];
+      if (validate && !isfinite(v)) atomicOr(&counters[1], 1);
+    } else {
+      const int wn = (c.n + 31) >> 5;
+      const uint32_t bit = (y[int64_t(f) * wn + (col >> 5)] >> (col & 31)) & 1u;
+      v = M(bit ? -mag[f] : mag[f]);
+    }
+  }
+  if (ok) lp[(int64_t(tile) * c.n + col) * kLanes + lane] = v;
+  const uint32_t b = __ballot_sync(kFull, ok && f < F && v < M(0));
+  if (ok && lane == 0) xh[int64_t(tile) * c.n + col] = uint8_t(b >> (threadIdx.x & 24));
+}
+
+// Alice's syndrome bits, one byte per (tile, stacked row) with bit = lane.
+__global__ void init_z_kernel(const DevCode c, int F, int n_tiles, const uint32_t* __restrict__ z,
+                              uint8_t* __restrict__ zt) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(n_tiles) * c.m_tot) return;
+  const int tile = int(idx / c.m_tot), r = int(idx % c.m_tot);
+  const int l = c.row_mat[r];
+  const int j = r - c.row_first[l];
+  int64_t off = 0;
+  for (int q = 0; q < l; ++q) off += int64_t(F) * ((c.m[q] + 31) >> 5);
+  const int wl = (c.m[l] + 31) >> 5;
+  uint32_t byte = 0;
+  for (int lane = 0; lane < kLanes; ++lane) {
+    const int f = tile * kLanes + lane;
+    if (f < F) byte |= ((z[off + int64_t(f) * wl + (j >> 5)] >> (j & 31)) & 1u) << lane;
+  }
+  zt[idx] = uint8_t(byte);
+}
+
+__global__ void init_tiles_kernel(int F, int n_tiles, int u, uint32_t* __restrict__ active,
+                                  uint32_t* __restrict__ fail) {
+  const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tile >= n_tiles) return;
+  const int left = F - tile * kLanes;
+  active[tile] = left >= kLanes ? 0xffu : ((1u << left) - 1u);
+  for (int l = 0; l < u; ++l) fail[tile * u + l] = 0;
+}
+
+// ------------------------------------------------------------- eq. (6)
+
+// One warp per slice (kSliceRows rows x kLanes frames), 8 slices per block.
+template <typename M, int DMAX>
+__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter, M* __restrict__ c2v,
+                                                 const M* __restrict__ lsrc, const uint8_t* __restrict__ zt,
+                                                 const uint32_t* __restrict__ active, M l_max) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int s = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (s >= c.n_slices) return;
+  const int lid = threadIdx.x & 31;
+  const int q = lid >> 3, lane = lid & 7;
+  const int r = s * kSliceRows + q;
+  const int base = c.slice_base[s];
+  const int deg = (c.slice_base[s + 1] - base) / kSliceRows;
+  const int64_t node0 = int64_t(tile) * c.n;
+  M* msg = c2v + int64_t(tile) * c.s_tot * kLanes;
+
+  M delta[DMAX], pre[DMAX];
+  uint64_t sgn = 0, valid = 0;
+  M P = M(0);
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) {
+    if (k < deg) {
+      const int slot = base + k * kSliceRows + q;
+      const int col = __ldg(c.slot_col + slot);
+      M d = M(0);
+      if (col >= 0) {
+        M v = __ldg(lsrc + (node0 + col) * kLanes + lane);
+        if (!first_iter) v -= msg[int64_t(slot) * kLanes + lane];
+        v = clampm(v, l_max);
+        sgn |= uint64_t(v < M(0)) << k;
+        valid |= uint64_t(1) << k;
+        d = Arith<M>::delta(fabs(v));
+      }
+      delta[k] = d;
+      pre[k] = P;
+      P = Arith<M>::oplus(P, d);
+    }
+  }
+  if (r >= c.m_tot || !((act >> lane) & 1u)) return;
+  const uint32_t z = (zt[int64_t(tile) * c.m_tot + r] >> lane) & 1u;
+  const uint32_t par = (__popcll(sgn) & 1u) ^ z;
+  M S = M(0);
+#pragma unroll
+  for (int k = DMAX - 1; k >= 0; --k) {
+    if (k < deg) {
+      if ((valid >> k) & 1u) {
+        const M D = Arith<M>::oplus(pre[k], S);
+        const M mag = fmin(Arith<M>::mag(D), l_max);
+        const uint32_t sk = par ^ uint32_t((sgn >> k) & 1u);
+        msg[int64_t(base + k * kSliceRows + q) * kLanes + lane] = sk ? -mag : mag;
+      }
+      S = Arith<M>::oplus(S, delta[k]);
+    }
+  }
+}
+
+// ------------------------------------------------------------- eq. (2)
+
+// Block: 32 variable nodes x 8 lanes. Sums in stacked-row order.
+template <typename M>
+__global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __restrict__ c2v, M* __restrict__ lv,
+                                                 const M* __restrict__ lp, uint8_t* __restrict__ xh,
+                                                 const uint32_t* __restrict__ active) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int lane = threadIdx.x & 7;
+  const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const bool ok = col < c.n;
+  const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
+  const M* msg = c2v + int64_t(tile) * c.s_tot * kLanes;
+  M sum = M(0);
+  if (ok) {
+    sum = lp[at];
+    const int a1 = c.col_ptr[col + 1];
+    for (int a = c.col_ptr[col]; a < a1; ++a) sum += msg[int64_t(__ldg(c.col_slot + a)) * kLanes + lane];
+    if ((act >> lane) & 1u) lv[at] = sum;
+  }
+  const uint32_t b = __ballot_sync(kFull, ok && sum < M(0));
+  if (ok && lane == 0) {
+    const uint32_t nb = (b >> (threadIdx.x & 24)) & 0xffu;
+    uint8_t* px = xh + int64_t(tile) * c.n + col;
+    *px = uint8_t((*px & ~act) | (nb & act));
+  }
+}
+
+// ------------------------------------------------------- stopping rule
+
+// One thread per (tile, stacked row): lanes whose hard decision breaks the row.
+__global__ void __launch_bounds__(256) syn_kernel(const DevCode c, const uint8_t* __restrict__ xh,
+                                                  const uint8_t* __restrict__ zt,
+                                                  const uint32_t* __restrict__ active, uint32_t* __restrict__ fail) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t bad = 0;
+  int l = -1;
+  if (r < c.m_tot) {
+    const uint8_t* x = xh + int64_t(tile) * c.n;
+    uint32_t p = zt[int64_t(tile) * c.m_tot + r];
+    const int e1 = c.row_ptr[r + 1];
+    for (int e = c.row_ptr[r]; e < e1; ++e) p ^= x[__ldg(c.col_idx + e)];
+    bad = p & act;
+    l = c.row_mat[r];
+  }
+  const int l0 = __shfl_sync(kFull, l, 0);
+  if (__all_sync(kFull, l == l0 || l < 0)) {
+    const uint32_t agg = __reduce_or_sync(kFull, bad);
+    if ((threadIdx.x & 31) == 0 && agg && l0 >= 0) atomicOr(&fail[tile * c.u + l0], agg);
+  } else if (bad) {
+    atomicOr(&fail[tile * c.u + l], bad);
+  }
+}
+
+// One thread per tile: retire lanes that satisfied every syndrome (or hit max_iter).
+__global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, int early_exit,
+                              uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
+                              int32_t* __restrict__ iters, uint8_t* __restrict__ success,
+                              uint8_t* __restrict__ synd_ok, int32_t* __restrict__ counters) {
+  const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tile >= n_tiles) return;
+  uint32_t act = active[tile];
+  if (act == 0) return;
+  uint32_t anyfail = 0;
+  for (int l = 0; l < u; ++l) anyfail |= fail[tile * u + l];
+  uint32_t done = 0;
+  if (t >= max_iter) done = act;
+  else if (early_exit) done = act & ~anyfail;
+  for (int lane = 0; lane < kLanes; ++lane) {
+    if (!((done >> lane) & 1u)) continue;
+    const int f = tile * kLanes + lane;
+    if (f >= F) continue;
+    iters[f] = t;
+    success[f] = uint8_t(!((anyfail >> lane) & 1u));
+    if (synd_ok)
+      for (int l = 0; l < u; ++l) synd_ok[int64_t(f) * u + l] = uint8_t(!((fail[tile * u + l] >> lane) & 1u));
+  }
+  act &= ~done;
+  active[tile] = act;
+  for (int l = 0; l < u; ++l) fail[tile * u + l] = 0;
+  if (act) atomicAdd(&counters[0], 1);
+}
+
+// ------------------------------------------------------------- outputs
+
+__global__ void out_bits_kernel(const DevCode c, int F, const uint8_t* __restrict__ xh, uint32_t* __restrict__ out) {
+  const int wn = (c.n + 31) >> 5;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(F) * wn) return;
+  const int f = int(idx / wn), w = int(idx % wn);
+  const int tile = f / kLanes, lane = f % kLanes;
+  const uint8_t* x = xh + int64_t(tile) * c.n;
+  uint32_t bits = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int i = w * 32 + b;
+    if (i >= c.n) break;
+    bits |= uint32_t((x[i] >> lane) & 1u) << b;
+  }
+  out[idx] = bits;
+}
+
+template <typename M>
+__global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv, const M* __restrict__ lp,
+                                const int32_t* __restrict__ iters, M* __restrict__ out) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(F) * c.n) return;
+  const int f = int(idx / c.n), i = int(idx % c.n);
+  const int64_t at = (int64_t(f / kLanes) * c.n + i) * kLanes + (f % kLanes);
+  out[idx] = iters[f] == 0 ? lp[at] : lv[at];
+}
+
+template <typename M>
+__global__ void export_c2v_kernel(const DevCode c, const M* __restrict__ c2v, int frame, M* __restrict__ out) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= c.e_tot) return;
+  const int tile = frame / kLanes, lane = frame % kLanes;
+  out[e] = c2v[(int64_t(tile) * c.s_tot + c.edge_slot[e]) * kLanes + lane];
+}
+
+// ------------------------------------------------------------- host side
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
+
+template <typename M, int DMAX>
+void launch_cn(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s) {
+  dim3 grid(blocks_for(c.n_slices, 8), st.n_tiles);
+  cn_kernel<M, DMAX><<<grid, 256, 0, s>>>(c, first_iter, static_cast<M*>(st.c2v),
+                                          static_cast<const M*>(first_iter ? st.lp : st.lv), st.zt, st.active,
+                                          M(l_max));
+}
+
+template <typename M>
+void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s) {
+  if (c.max_row_deg <= 8) launch_cn<M, 8>(c, st, first_iter, l_max, s);
+  else if (c.max_row_deg <= 16) launch_cn<M, 16>(c, st, first_iter, l_max, s);
+  else if (c.max_row_deg <= 32) launch_cn<M, 32>(c, st, first_iter, l_max, s);
+  else launch_cn<M, 64>(c, st, first_iter, l_max, s);
+}
+
+template <typename M>
+int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s) {
+  cudaError_t e;
+#define CK(call, what) \
+  if ((e = (call)) != cudaSuccess) return cuda_error(e, what)
+#define CKL(what) CK(cudaGetLastError(), what)
+  const int F = st.F, NT = st.n_tiles;
+  CK(cudaMemsetAsync(st.counters, 0, 4 * sizeof(int32_t), s), "clear counters");
+  prof_begin(MBP_KERNEL_SETUP, s);
+  if (a.y_bits) {
+    frame_mag_kernel<<<blocks_for(F, 256), 256, 0, s>>>(a.qber, F, st.llr_mag);
+    CKL("frame_mag_kernel");
+  }
+  init_lp_kernel<M><<<dim3(blocks_for(c.n, 32), NT), 256, 0, s>>>(
+      c, F, static_cast<const M*>(a.llr), a.y_bits, st.llr_mag, static_cast<M*>(st.lp), st.xh, st.counters,
+      a.validate);
+  CKL("init_lp_kernel");
+  init_z_kernel<<<blocks_for(int64_t(NT) * c.m_tot, 256), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt);
+  CKL("init_z_kernel");
+  init_tiles_kernel<<<blocks_for(NT, 256), 256, 0, s>>>(F, NT, c.u, st.active, st.fail);
+  CKL("init_tiles_kernel");
+  prof_end(MBP_KERNEL_SETUP, s, a.y_bits ? 4 : 3);
+  int32_t host_ctr[4];
+  if (a.validate) {
+    CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof host_ctr, cudaMemcpyDeviceToHost, s), "read validate flag");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (host_ctr[1]) return set_error(MBP_EINVAL, "llr holds a non-finite value");
+  }
+  const dim3 syn_grid(blocks_for(c.m_tot, 256), NT);
+  auto stop_check = [&](int t, int* left) -> int {
+    prof_begin(MBP_KERNEL_SYNDROME, s);
+    syn_kernel<<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    CKL("syn_kernel");
+    prof_end(MBP_KERNEL_SYNDROME, s, 1);
+    CK(cudaMemsetAsync(st.counters, 0, sizeof(int32_t), s), "clear counter");
+    prof_begin(MBP_KERNEL_RETIRE, s);
+    update_kernel<<<blocks_for(NT, 128), 128, 0, s>>>(F, NT, c.u, t, a.max_iter, a.early_exit, st.active, st.fail,
+                                                       a.iters, a.success, a.synd_ok, st.counters);
+    CKL("update_kernel");
+    prof_end(MBP_KERNEL_RETIRE, s, 1);
+    CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read counter");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *left = host_ctr[0];
+    return MBP_OK;
+  };
+  int left = NT;
+  int rc;
+  if (a.early_exit || a.max_iter == 0) {
+    if ((rc = stop_check(0, &left))) return rc;
+  }
+  for (int t = 1; t <= a.max_iter && left > 0; ++t) {
+    prof_begin(MBP_KERNEL_CHECK, s);
+    launch_cn_any<M>(c, st, t == 1, a.l_max, s);
+    CKL("cn_kernel");
+    prof_end(MBP_KERNEL_CHECK, s, 1);
+    prof_begin(MBP_KERNEL_VARIABLE, s);
+    vn_kernel<M><<<dim3(blocks_for(c.n, 32), NT), 256, 0, s>>>(c, static_cast<const M*>(st.c2v),
+                                                               static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
+                                                               st.xh, st.active);
+    CKL("vn_kernel");
+    prof_end(MBP_KERNEL_VARIABLE, s, 1);
+    if (a.early_exit || t == a.max_iter) {
+      if ((rc = stop_check(t, &left))) return rc;
+    }
+  }
+  const int wn = (c.n + 31) >> 5;
+  prof_begin(MBP_KERNEL_OUTPUT, s);
+  out_bits_kernel<<<blocks_for(int64_t(F) * wn, 256), 256, 0, s>>>(c, F, st.xh, a.x_hat_bits);
+  CKL("out_bits_kernel");
+  if (a.soft_out) {
+    soft_out_kernel<M><<<blocks_for(int64_t(F) * c.n, 256), 256, 0, s>>>(
+        c, F, static_cast<const M*>(st.lv), static_cast<const M*>(st.lp), a.iters, static_cast<M*>(a.soft_out));
+    CKL("soft_out_kernel");
+  }
+  prof_end(MBP_KERNEL_OUTPUT, s, a.soft_out ? 2 : 1);
+#undef CKL
+#undef CK
+  return MBP_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_syndrome(const DevCode& c, const uint32_t* x_bits, int F, uint32_t* z_bits, cudaStream_t s) {
+  int64_t off = 0;
+  for (int l = 0; l < c.u; ++l) {
+    const int wl = (c.m[l] + 31) >> 5;
+    const int64_t work = int64_t(F) * wl;
+    if (work > 0) syndrome_kernel<<<blocks_for(work, 128), 128, 0, s>>>(c, l, x_bits, F, z_bits + off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    off += work;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_bsc_llr(const uint32_t* y_bits, const double* qber, int F, int n, int dtype, void* llr,
+                           cudaStream_t s) {
+  dim3 grid(blocks_for(n, 256), F);
+  if (dtype == MBP_MSG_F64) bsc_llr_kernel<double><<<grid, 256, 0, s>>>(y_bits, qber, n, static_cast<double*>(llr));
+  else bsc_llr_kernel<float><<<grid, 256, 0, s>>>(y_bits, qber, n, static_cast<float*>(llr));
+  return cudaGetLastError();
+}
+
+static size_t msg_size(int msg_dtype) { return msg_dtype == MBP_MSG_F64 ? 8 : 4; }
+
+static void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, size_t* total) {
+  const size_t NT = (size_t(F) + kLanes - 1) / kLanes;
+  const size_t ms = msg_size(msg_dtype);
+  const size_t wn = (size_t(c.n) + 31) / 32;
+  size_t zw = 0;
+  for (int l = 0; l < c.u; ++l) zw += (size_t(c.m[l]) + 31) / 32;
+  const size_t sizes[] = {
+      NT * size_t(c.s_tot) * kLanes * ms,  // c2v
+      NT * size_t(c.n) * kLanes * ms,      // lv
+      NT * size_t(c.n) * kLanes * ms,      // lp
+      NT * size_t(c.n),                    // xh
+      NT * size_t(c.m_tot),                // zt
+      NT * 4,                              // active
+      NT * size_t(c.u) * 4,                // fail
+      size_t(F) * 8,                       // llr_mag
+      16,                                  // counters
+      host_io ? size_t(F) * wn * 4 : 0,    // io_y
+      host_io ? size_t(F) * 8 : 0,         // io_qber
+      host_io ? size_t(F) * zw * 4 : 0,    // io_z
+      host_io ? size_t(F) * wn * 4 : 0,    // io_xhat
+      host_io ? size_t(F) * 4 : 0,         // io_iters
+      host_io ? size_t(F) : 0,             // io_success
+  };
+  size_t t = 0;
+  for (int i = 0; i < 15; ++i) {
+    offs[i] = t;
+    t += align256(sizes[i]);
+  }
+  *total = t;
+}
+
+size_t workspace_bytes(const DevCode& c, int F, int msg_dtype, bool host_io) {
+  size_t offs[15], total;
+  layout(c, F, msg_dtype, host_io, offs, &total);
+  return total;
+}
+
+void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void* base, DevState* st) {
+  size_t o[15], total;
+  layout(c, F, msg_dtype, host_io, o, &total);
+  char* b = static_cast<char*>(base);
+  st->F = F;
+  st->n_tiles = (F + kLanes - 1) / kLanes;
+  st->c2v = b + o[0];
+  st->lv = b + o[1];
+  st->lp = b + o[2];
+  st->xh = reinterpret_cast<uint8_t*>(b + o[3]);
+  st->zt = reinterpret_cast<uint8_t*>(b + o[4]);
+  st->active = reinterpret_cast<uint32_t*>(b + o[5]);
+  st->fail = reinterpret_cast<uint32_t*>(b + o[6]);
+  st->llr_mag = reinterpret_cast<double*>(b + o[7]);
+  st->counters = reinterpret_cast<int32_t*>(b + o[8]);
+  st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[9]) : nullptr;
+  st->io_qber = host_io ? reinterpret_cast<double*>(b + o[10]) : nullptr;
+  st->io_z = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;
+  st->io_xhat = host_io ? reinterpret_cast<uint32_t*>(b + o[12]) : nullptr;
+  st->io_iters = host_io ? reinterpret_cast<int32_t*>(b + o[13]) : nullptr;
+  st->io_success = host_io ? reinterpret_cast<uint8_t*>(b + o[14]) : nullptr;
+}
+
+int decode(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {
+  if (st.n_tiles > 65535) return set_error(MBP_EUNSUPPORTED, "F = %d exceeds %d frames per call", st.F, 65535 * kLanes);
+  return msg_dtype == MBP_MSG_F64 ? decode_t<double>(c, st, a, s) : decode_t<float>(c, st, a, s);
+}
+
+cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtype, int frame, void* out,
+                              cudaStream_t s) {
+  if (c.e_tot == 0) return cudaSuccess;
+  if (msg_dtype == MBP_MSG_F64)
+    export_c2v_kernel<double><<<blocks_for(c.e_tot, 256), 256, 0, s>>>(c, static_cast<const double*>(st.c2v), frame,
+                                                                         static_cast<double*>(out));
+  else
+    export_c2v_kernel<float><<<blocks_for(c.e_tot, 256), 256, 0, s>>>(c, static_cast<const float*>(st.c2v), frame,
+                                                                        static_cast<float*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace mbp

@@ -1,0 +1,315 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GB300).
+
+Acceptance, per the decoder's contract:
+  * syndromes (eq. 1), output bits, success flags and per-matrix syndrome
+    passes are bit-exact on every frame where the oracle converges;
+  * FP32 messages and posteriors are within 1e-3 of the FP64 oracle for
+    iterations 1..5, FP64 ones within 1e-9;
+  * iteration counts are compared and reported as a diagnostic (FP32 may take
+    a different path near a decision boundary), and are exact in FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import mbp_inputs as mi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-3
+TOL_F64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def mbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_07979_gb300 as m
+    m.build()
+    return m
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def u32_to_i32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)
+
+
+def host_u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+class Workload:
+    def __init__(self, n, m, dist, u, seed, F, qber, fseed=0, depth_cap=None):
+        self.n, self.F = n, F
+        self.H = mi.make_codes(n, m, dist, u, seed, depth_cap=depth_cap)
+        self.x, self.y, self.e = mi.bsc_frames(n, F, qber, seed=seed * 1000 + fseed)
+        self.z_orc = orc.syndrome(self.H, self.x)
+
+
+def gpu_syndrome(mbp, codes, x):
+    return mbp.mbp_syndrome(codes, dev(u32_to_i32(x)))
+
+
+def check_outputs_bit_exact(out, ref, n, fp64=False):
+    xh = host_u32(out["x_hat_bits"])
+    it = out["iters"].cpu().numpy()
+    ok = out["success"].cpu().numpy()
+    conv = ref["success"].astype(bool)
+    assert np.array_equal(ok[conv], ref["success"][conv]), "success flags differ where the oracle converged"
+    assert np.array_equal(xh[conv], ref["x_hat_bits"][conv]), "output bits differ where the oracle converged"
+    if "synd_ok" in out and "synd_ok" in ref:
+        so = out["synd_ok"].cpu().numpy()
+        assert np.array_equal(so[conv], ref["synd_ok"][conv])
+    if fp64:
+        assert np.array_equal(it, ref["iters"])
+        assert np.array_equal(ok, ref["success"]) and np.array_equal(xh, ref["x_hat_bits"])
+    return int(np.sum(it[conv] != ref["iters"][conv]))
+
+
+# ---------------------------------------------------------------- eq. (1)
+
+@pytest.mark.parametrize("spec", [(1024, 512, {3: 1.0}, 2, 0, 64), (1000, 333, {2: 0.5, 3: 0.5}, 3, 5, 13),
+                                  (65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 9)])
+def test_syndrome_bit_exact(mbp, spec):
+    n, m, dist, u, seed, F = spec
+    w = Workload(n, m, dist, u, seed, F, 0.03)
+    codes = mbp.mbp_create_codes(w.H)
+    z = host_u32(gpu_syndrome(mbp, codes, w.x))
+    assert np.array_equal(z, np.concatenate([a.reshape(-1) for a in w.z_orc]))
+
+
+# ---------------------------------------------------------------- eq. (5)
+
+def test_bsc_llr_matches_oracle(mbp):
+    n, F = 1000, 11
+    _, y, _ = mi.bsc_frames(n, F, 0.02, seed=4)
+    e = np.linspace(0.001, 0.2, F)
+    ref = orc.bsc_llr(y, n, e)
+    l32 = mbp.mbp_bsc_llr(dev(u32_to_i32(y)), dev(e), n, torch.float32).cpu().numpy()
+    l64 = mbp.mbp_bsc_llr(dev(u32_to_i32(y)), dev(e), n, torch.float64).cpu().numpy()
+    assert np.allclose(l64, ref, rtol=0, atol=1e-13)
+    assert np.allclose(l32, ref, rtol=0, atol=1e-6)
+
+
+# ------------------------------------------------------- whole decoder
+
+def _decode_both(mbp, w, max_iter, msg64, early_exit=True, want_lv=False, threads=8):
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y = dev(u32_to_i32(w.y))
+    e = dev(w.e)
+    out = mbp.mbp_decode_bsc(codes, y, e, z, max_iter, msg_dtype=mbp.MSG_F64 if msg64 else mbp.MSG_F32,
+                             early_exit=early_exit, want_soft=want_lv, want_synd=True)
+    torch.cuda.synchronize()
+    ref = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, max_iter, early_exit=early_exit, threads=threads,
+                     want_lv=want_lv, want_synd=True)
+    return codes, out, ref
+
+
+@pytest.mark.parametrize("msg64", [True, False])
+def test_rate05_n1024_u2_qber3(mbp, msg64):
+    """n=1024, m=512 per matrix, d_v=3, u=2, QBER 3%, 64 frames, max 50 iterations, seed 0."""
+    w = Workload(1024, 512, {3: 1.0}, 2, 0, 64, 0.03)
+    _, out, ref = _decode_both(mbp, w, 50, msg64, want_lv=True)
+    check_outputs_bit_exact(out, ref, w.n, fp64=msg64)
+    assert ref["success"].all()
+    if msg64:
+        assert np.allclose(out["soft"].cpu().numpy(), ref["L_V"], atol=TOL_F64)
+
+
+@pytest.mark.parametrize("msg64", [True, False])
+@pytest.mark.parametrize("t", [1, 2, 3, 4, 5])
+def test_messages_within_tolerance_first_iterations(mbp, msg64, t):
+    """C2V and L_V after t flooding iterations (no early exit), 13 frames = 2 tiles with a ragged tail."""
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 13, 0.05)
+    codes, out, ref = _decode_both(mbp, w, t, msg64, early_exit=False, want_lv=True)
+    tol = TOL_F64 if msg64 else TOL_F32
+    ref_c2v = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, t, early_exit=False, want_c2v=True)["c2v"]
+    assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= tol
+    for f in range(w.F):
+        c = mbp.mbp_export_c2v(codes, w.F, out["workspace"], f, mbp.MSG_F64 if msg64 else mbp.MSG_F32)
+        assert np.max(np.abs(c.cpu().numpy() - ref_c2v[f])) <= tol, f
+    assert np.array_equal(out["iters"].cpu().numpy(), np.full(w.F, t))
+
+
+def test_rate07_n65536_first_iterations_fp32(mbp):
+    """The n=65536 rate-0.7 code: FP32 C2V/L_V within 1e-3 of the oracle over iterations 1..5."""
+    w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 3, 0.02)
+    LP = orc.bsc_llr(w.y, w.n, w.e)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    for t in range(1, 6):
+        out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y)), dev(w.e), z, t, early_exit=False, want_soft=True)
+        ref = orc.decode(w.H, LP, w.z_orc, t, early_exit=False, want_lv=True, want_c2v=True, threads=3)
+        assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= TOL_F32
+        for f in range(w.F):
+            c = mbp.mbp_export_c2v(codes, w.F, out["workspace"], f).cpu().numpy()
+            assert np.max(np.abs(c - ref["c2v"][f])) <= TOL_F32
+
+
+def test_rate07_n65536_subset_bit_exact(mbp):
+    """n=65536, R=0.7, d_v {2,3,8}, u=2, QBER 2%: 64 frames, max 60 iterations."""
+    w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 64, 0.02)
+    _, out, ref = _decode_both(mbp, w, 60, False)
+    mism = check_outputs_bit_exact(out, ref, w.n)
+    assert ref["success"].all() and mism <= 1
+    assert np.array_equal(host_u32(out["x_hat_bits"]), w.x)
+
+
+@pytest.mark.slow
+def test_rate07_n65536_full_batch_sampled(mbp):
+    """All 1024 frames in the benchmark's launch configuration; oracle on a sample of frames,
+    invariants (success => every syndrome holds, converged => Alice's key) on every frame."""
+    F = 1024
+    H = mi.make_codes(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1)
+    x, y, e = mi.bsc_frames(65536, F, 0.02, seed=1)
+    codes = mbp.mbp_create_codes(H)
+    z = gpu_syndrome(mbp, codes, x)
+    out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(y)), dev(e), z, 60, want_synd=True)
+    xh = host_u32(out["x_hat_bits"])
+    ok = out["success"].cpu().numpy().astype(bool)
+    zo = orc.syndrome(H, xh)
+    zz = orc.syndrome(H, x)
+    for l in range(2):
+        sat = np.all(zo[l] == zz[l], axis=1)
+        assert np.all(sat[ok])
+    assert np.array_equal(xh[ok], x[ok])
+    sample = np.arange(0, F, 97)
+    ref = orc.decode(H, orc.bsc_llr(y[sample], 65536, e[sample]), [a[sample] for a in zz], 60, threads=8)
+    assert np.array_equal(ref["x_hat_bits"], xh[sample])
+    assert np.array_equal(ref["success"], out["success"].cpu().numpy()[sample])
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_edge_cases(mbp):
+    # n not a multiple of 32, u = 3, one frame, degree-1 and degree-0 checks
+    n = 77
+    H = mi.make_codes(n, 30, {2: 0.5, 3: 0.5}, 3, 21)
+    # append a degree-1 check and an empty check to matrix 0
+    h0 = H[0]
+    rp = np.concatenate([h0.row_ptr, [h0.row_ptr[-1] + 1, h0.row_ptr[-1] + 1]]).astype(np.int32)
+    ci = np.concatenate([h0.col_idx, [5]]).astype(np.int32)
+    H[0] = mi.CSR(n, h0.m + 2, rp, ci)
+    x, y, e = mi.bsc_frames(n, 1, 0.05, seed=2)
+    z = orc.syndrome(H, x)
+    codes = mbp.mbp_create_codes(H)
+    zg = gpu_syndrome(mbp, codes, x)
+    assert np.array_equal(host_u32(zg), np.concatenate([a.reshape(-1) for a in z]))
+    for msg64 in (True, False):
+        out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(y)), dev(e), zg, 20, want_synd=True, want_soft=True,
+                                 msg_dtype=mbp.MSG_F64 if msg64 else mbp.MSG_F32)
+        ref = orc.decode(H, orc.bsc_llr(y, n, e), z, 20, want_synd=True, want_lv=True)
+        check_outputs_bit_exact(out, ref, n, fp64=msg64)
+
+
+def test_empty_batch_and_zero_iterations(mbp):
+    w = Workload(512, 200, {3: 1.0}, 2, 3, 9, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y = dev(u32_to_i32(w.y))
+    out = mbp.mbp_decode_bsc(codes, y[:0], dev(w.e)[:0], z[:0], 10)
+    assert out["iters"].numel() == 0
+    for early in (True, False):
+        out = mbp.mbp_decode_bsc(codes, y, dev(w.e), z, 0, early_exit=early, want_synd=True, want_soft=True)
+        ref = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, 0, early_exit=early, want_synd=True, want_lv=True)
+        check_outputs_bit_exact(out, ref, w.n, fp64=True)
+        assert np.allclose(out["soft"].cpu().numpy(), ref["L_V"], atol=1e-6)
+
+
+def test_noise_free_frames_stop_at_iteration_zero(mbp):
+    w = Workload(512, 200, {3: 1.0}, 2, 3, 10, 0.0)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y)), dev(np.full(10, 0.02)), z, 10)
+    assert out["iters"].cpu().numpy().tolist() == [0] * 10
+    assert np.array_equal(host_u32(out["x_hat_bits"]), w.x)
+
+
+def test_failing_frames_fp64_match_oracle(mbp):
+    """Above the decoding threshold: failures report success=0, iters=max_iter, last hard decision."""
+    w = Workload(1024, 512, {3: 1.0}, 2, 0, 16, 0.2)
+    _, out, ref = _decode_both(mbp, w, 15, True)
+    check_outputs_bit_exact(out, ref, w.n, fp64=True)
+    assert (ref["success"] == 0).any()
+
+
+def test_single_matrix_u1(mbp):
+    w = Workload(2048, 1024, {3: 1.0}, 1, 8, 16, 0.05)
+    _, out, ref = _decode_both(mbp, w, 40, True)
+    check_outputs_bit_exact(out, ref, w.n, fp64=True)
+
+
+def test_llr_entry_matches_bsc_entry(mbp):
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 21, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y, e = dev(u32_to_i32(w.y)), dev(w.e)
+    a = mbp.mbp_decode_bsc(codes, y, e, z, 30)
+    llr = mbp.mbp_bsc_llr(y, e, w.n, torch.float32)
+    b = mbp.mbp_decode_batch(codes, llr, z, 30, validate=True)
+    for k in ("x_hat_bits", "iters", "success"):
+        assert torch.equal(a[k], b[k])
+
+
+def test_host_io_entry_matches_device_entry(mbp):
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 21, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    a = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y)), dev(w.e), z, 30)
+    zh = z.cpu().numpy().view(np.uint32)
+    b = mbp.mbp_decode_bsc_host(codes, w.y, w.e, zh, 30)
+    assert np.array_equal(host_u32(a["x_hat_bits"]), b["x_hat_bits"])
+    assert np.array_equal(a["iters"].cpu().numpy(), b["iters"])
+    assert np.array_equal(a["success"].cpu().numpy(), b["success"])
+
+
+def test_invalid_arguments_return_errors(mbp):
+    w = Workload(512, 200, {3: 1.0}, 2, 3, 8, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y, e = dev(u32_to_i32(w.y)), dev(w.e)
+    llr = mbp.mbp_bsc_llr(y, e, w.n, torch.float32)
+    bad = llr.clone()
+    bad[3, 7] = float("nan")
+    with pytest.raises(mbp.MBPError) as ei:
+        mbp.mbp_decode_batch(codes, bad, z, 10, validate=True)
+    assert ei.value.status == 1
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    lib = mbp._load()
+    o = mbp._opts(mbp.MSG_F32, 20.0, True, False, False, small)
+    xh = torch.empty((8, 16), dtype=torch.int32, device="cuda")
+    it = torch.empty(8, dtype=torch.int32, device="cuda")
+    ok = torch.empty(8, dtype=torch.uint8, device="cuda")
+    import ctypes
+    rc = lib.mbp_decode_batch(codes.handle, 8, llr.data_ptr(), z.data_ptr(), 10, ctypes.byref(o), xh.data_ptr(),
+                              it.data_ptr(), ok.data_ptr(), None)
+    assert rc == 1 and b"workspace too small" in lib.mbp_last_error_string()
+    host = np.zeros(8, np.int32)
+    ws = torch.empty(mbp.mbp_decode_workspace_size(codes, 8), dtype=torch.uint8, device="cuda")
+    o = mbp._opts(mbp.MSG_F32, 20.0, True, False, False, ws)
+    rc = lib.mbp_decode_batch(codes.handle, 8, llr.data_ptr(), z.data_ptr(), 10, ctypes.byref(o), xh.data_ptr(),
+                              host.ctypes.data, ok.data_ptr(), None)
+    assert rc == 1 and b"iters" in lib.mbp_last_error_string()
+    o.l_max = -1.0
+    rc = lib.mbp_decode_batch(codes.handle, 8, llr.data_ptr(), z.data_ptr(), 10, ctypes.byref(o), xh.data_ptr(),
+                              it.data_ptr(), ok.data_ptr(), None)
+    assert rc == 1
+
+
+def test_workspace_reuse_across_calls(mbp):
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 16, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y, e = dev(u32_to_i32(w.y)), dev(w.e)
+    a = mbp.mbp_decode_bsc(codes, y, e, z, 30)
+    b = mbp.mbp_decode_bsc(codes, y, e, z, 30, workspace=a["workspace"])
+    for k in ("x_hat_bits", "iters", "success"):
+        assert torch.equal(a[k], b[k])
