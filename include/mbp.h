@@ -175,6 +175,36 @@ int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int fram
                    mbp_stream_t stream);
 
 /*
+ * Allocation-free decode. The paper has no counterpart: this entry point
+ * exists for callers that can pass device inputs and outputs but cannot call
+ * cudaMalloc for a workspace, for example because another runtime owns the
+ * device memory budget, or because an allocation (and the device
+ * synchronization that cudaFree implies) is not allowed where they call from.
+ *
+ * It behaves like mbp_decode_bsc, but keeps the decoder state in a fixed
+ * device array of MBP_STATIC_SCRATCH_BYTES inside this library instead of
+ * opts->workspace. opts->workspace and opts->workspace_bytes are ignored, and
+ * opts->host_io must be 0. The call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *  - The array is created when the library's device code is loaded on a GPU.
+ *    Every GPU that loads the library holds it until the process exits.
+ *  - The first call on each device looks up the array's device address, with
+ *    that device current, and caches it. Make that first call before starting
+ *    any stream capture.
+ *  - Sizes: a batch whose workspace (mbp_decode_workspace_size with the same
+ *    opts) exceeds MBP_STATIC_SCRATCH_BYTES is rejected with MBP_EINVAL.
+ *  - Every call shares the one array and leaves its contents behind. The
+ *    decoder initialises everything it reads, so a call never sees the
+ *    previous call's state. Two calls whose GPU work overlaps, for example on
+ *    two streams or two host threads, race on the array and give undefined
+ *    results: serialise them.
+ */
+#define MBP_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                          const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                          int32_t* iters, uint8_t* success, mbp_stream_t stream);
+
+/*
  * Kernel accounting for benchmarks (no counterpart in the paper). While
  * enabled on a host thread, the decode calls made by that thread record a CUDA
  * event pair on the call's stream around every kernel they launch and add the

@@ -465,6 +465,51 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   return MBP_OK;
 }
 
+int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                          const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                          int32_t* iters, uint8_t* success, mbp_stream_t stream) {
+  g_err.clear();
+  REQUIRE(codes, "codes is NULL");
+  REQUIRE(F >= 0, "F must be >= 0");
+  REQUIRE(max_iter >= 0 && max_iter <= 1000000, "max_iter must be in [0, 1e6]");
+  if (F == 0) return MBP_OK;
+  int rc = validate_opts(opts);
+  if (rc) return rc;
+  REQUIRE(opts->host_io == 0, "opts->host_io must be 0 for mbp_decode_bsc_static");
+  const size_t need = workspace_bytes(codes->d, F, opts->msg_dtype, false);
+  REQUIRE(need <= MBP_STATIC_SCRATCH_BYTES,
+          "F = %d needs %zu bytes of decoder state, more than the %u bytes of static scratch", F, need,
+          MBP_STATIC_SCRATCH_BYTES);
+  REQUIRE(y_bits && qber, "y_bits and qber must be non-NULL");
+  REQUIRE_DEV(y_bits, "y_bits");
+  REQUIRE_DEV(qber, "qber");
+  REQUIRE_DEV(z_bits, "z_bits");
+  REQUIRE_DEV(x_hat_bits, "x_hat_bits");
+  REQUIRE_DEV(iters, "iters");
+  REQUIRE_DEV(success, "success");
+  if (opts->soft_out) REQUIRE_DEV(opts->soft_out, "opts->soft_out");
+  if (opts->synd_ok) REQUIRE_DEV(opts->synd_ok, "opts->synd_ok");
+  void* scratch = nullptr;
+  rc = static_scratch(&scratch);
+  if (rc) return rc;
+  DevState st;
+  carve_workspace(codes->d, F, opts->msg_dtype, false, scratch, &st);
+  DecodeArgs a{};
+  a.y_bits = y_bits;
+  a.qber = qber;
+  a.z_bits = z_bits;
+  a.max_iter = max_iter;
+  a.early_exit = opts->early_exit;
+  a.validate = 0;
+  a.l_max = opts->l_max;
+  a.x_hat_bits = x_hat_bits;
+  a.iters = iters;
+  a.success = success;
+  a.soft_out = opts->soft_out;
+  a.synd_ok = opts->synd_ok;
+  return decode(codes->d, st, opts->msg_dtype, a, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int frame, void* c2v_out,
                    mbp_stream_t stream) {
   g_err.clear();

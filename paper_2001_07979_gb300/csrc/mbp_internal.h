@@ -27,6 +27,7 @@ constexpr int kLanes = 8;       // frames interleaved per tile
 constexpr int kSliceRows = 4;   // rows per slice: one warp = kSliceRows rows x kLanes frames
 constexpr int kMaxU = 16;
 constexpr int kMaxRowDeg = 64;
+constexpr int kMaxDevices = 64;
 
 struct DevCode {
   int32_t n, u, m_tot, n_slices;
@@ -113,5 +114,7 @@ void prof_end(int family, cudaStream_t s, int kernels);
 int prof_get(int family, int64_t* launches, double* ms);
 cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtype, int frame, void* out,
                               cudaStream_t s);
+// address of the library's fixed device scratch on the current device (mbp_decode_bsc_static)
+int static_scratch(void** ptr);
 
 }  // namespace mbp

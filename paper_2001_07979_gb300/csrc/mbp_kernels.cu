@@ -20,8 +20,14 @@
 // (+)-combinations, never a division. Per edge this is two MUFU operations in,
 // two out (exp + reciprocal, reciprocal + log).
 #include <cstdio>
+#include <mutex>
 
 #include "mbp_internal.h"
+
+// Fixed device scratch of mbp_decode_bsc_static: the decoder state of one call,
+// for callers that must not allocate. Every GPU that loads this library holds
+// these bytes until the process exits; every call shares them.
+static __device__ __align__(256) unsigned char g_static_scratch[MBP_STATIC_SCRATCH_BYTES];
 
 namespace mbp {
 namespace {
@@ -537,6 +543,27 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
 int decode(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {
   if (st.n_tiles > 65535) return set_error(MBP_EUNSUPPORTED, "F = %d exceeds %d frames per call", st.F, 65535 * kLanes);
   return msg_dtype == MBP_MSG_F64 ? decode_t<double>(c, st, a, s) : decode_t<float>(c, st, a, s);
+}
+
+// Device address of g_static_scratch on the current device. Host code only holds
+// a stand-in for the array's name, so the address is looked up once per device
+// (with that device current) and cached.
+int static_scratch(void** ptr) {
+  static std::mutex mu;
+  static void* addr[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return set_error(MBP_EUNSUPPORTED, "device %d beyond %d devices", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the static scratch");
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return MBP_OK;
 }
 
 cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtype, int frame, void* out,

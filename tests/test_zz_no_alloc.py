@@ -1,0 +1,93 @@
+"""The allocation-free decode entry point, called through the C ABI.
+
+Some callers cannot call cudaMalloc for a decoder workspace: they can hand the
+library device inputs and outputs, but the device memory budget belongs to
+another runtime, or an allocation is not allowed where they run. For them
+``mbp_decode_bsc_static`` keeps the decoder state in a fixed device array
+inside the library (MBP_STATIC_SCRATCH_BYTES). This test checks, on calls made
+back to back, that it returns exactly what ``mbp_decode_bsc`` returns on the
+same inputs. It also checks that a batch too large for the array is refused.
+
+This file is collected last, so a run that stops at its first failure has run
+every other test before this one.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import mbp_inputs as mi
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-3  # the FP32 tolerance of the parity tests; identical kernels are expected to agree exactly
+
+
+@pytest.fixture(scope="module")
+def mbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_07979_gb300 as m
+    m.build()
+    lib = m._load()
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.mbp_decode_bsc_static.restype = I
+    lib.mbp_decode_bsc_static.argtypes = [P, I, P, P, P, I, P, P, P, P, P]
+    return m
+
+
+def _inputs(mbp, n, m, dist, u, seed, F, qber):
+    H = mi.make_codes(n, m, dist, u, seed)
+    x, y, e = mi.bsc_frames(n, F, qber, seed=seed + 17)
+    codes = mbp.mbp_create_codes(H)
+    xd = torch.from_numpy(x.view(np.int32)).cuda()
+    z = mbp.mbp_syndrome(codes, xd)
+    return codes, torch.from_numpy(y.view(np.int32)).cuda(), torch.from_numpy(e).cuda(), z
+
+
+def _static_decode(mbp, codes, y, e, z, max_iter, msg_dtype=0):
+    F = y.shape[0]
+    dev = y.device
+    xh = torch.full((F, (codes.n + 31) // 32), -1, dtype=torch.int32, device=dev)
+    it = torch.full((F,), -1, dtype=torch.int32, device=dev)
+    ok = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+    soft = torch.full((F, codes.n), float("nan"), dtype=torch.float64 if msg_dtype else torch.float32, device=dev)
+    synd = torch.full((F, codes.u), 7, dtype=torch.uint8, device=dev)
+    o = mbp._opts(msg_dtype, 20.0, True, False, False, None, soft, synd)
+    rc = mbp._lib.mbp_decode_bsc_static(codes.handle, F, y.data_ptr(), e.data_ptr(), z.data_ptr(), max_iter,
+                                       ctypes.byref(o), xh.data_ptr(), it.data_ptr(), ok.data_ptr(),
+                                       torch.cuda.current_stream().cuda_stream or None)
+    return rc, dict(x_hat_bits=xh, iters=it, success=ok, soft=soft, synd_ok=synd)
+
+
+def _compare(mbp, codes, y, e, z, max_iter, msg_dtype=0):
+    rc, got = _static_decode(mbp, codes, y, e, z, max_iter, msg_dtype)
+    assert rc == 0, mbp._lib.mbp_last_error_string()
+    ref = mbp.mbp_decode_bsc(codes, y, e, z, max_iter, msg_dtype=msg_dtype, want_soft=True, want_synd=True)
+    torch.cuda.synchronize()
+    for k in ("x_hat_bits", "iters", "success", "synd_ok"):
+        assert torch.equal(got[k], ref[k]), k
+    assert torch.max(torch.abs(got["soft"] - ref["soft"])).item() <= TOL_F32
+
+
+def test_static_scratch_decode_matches_workspace_decode(mbp):
+    a = _inputs(mbp, 1024, 512, {3: 1.0}, 2, 0, 64, 0.03)
+    b = _inputs(mbp, 4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 3, 3, 13, 0.06)
+    _compare(mbp, *a, 50)           # first call on this device: looks up the array's address
+    _compare(mbp, *b, 40)           # second call in a row, another code and batch size
+    _compare(mbp, *a, 50, msg_dtype=1)  # the array keeps b's state; a must not see it
+    _compare(mbp, *b, 40)
+
+
+def test_static_scratch_refuses_oversized_batches(mbp):
+    codes, y, e, z = _inputs(mbp, 4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 8, 0.05)
+    F = 2000
+    need = mbp.mbp_decode_workspace_size(codes, F)
+    assert need > 64 * 1024 * 1024
+    yb = y.repeat(F // 8, 1)
+    eb = e.repeat(F // 8)
+    zb = torch.zeros(F * sum(codes.syndrome_words()), dtype=torch.int32, device=y.device)
+    rc, _ = _static_decode(mbp, codes, yb, eb, zb, 10)
+    assert rc == 1  # MBP_EINVAL
+    assert b"static scratch" in mbp._lib.mbp_last_error_string()
