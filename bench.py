@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--frames", type=int, default=FRAMES)
     p.add_argument("--cpu-sample", type=int, default=256, help="frames in the oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--accumulate", default="auto", choices=["auto", "float", "fixed"],
+                   help="eq. (2) accumulation: fixed-point single pass or float second pass")
     return p.parse_args()
 
 
@@ -212,8 +214,11 @@ def run_gb300(args):
     ws = torch.empty(mbp.mbp_decode_workspace_size(codes, F, mbp.MSG_F32), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    acc = {"auto": mbp.ACC_AUTO, "float": mbp.ACC_FLOAT, "fixed": mbp.ACC_FIXED}[args.accumulate]
+
     def step():
-        return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=mbp.MSG_F32, l_max=L_MAX, workspace=ws)
+        return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=mbp.MSG_F32, l_max=L_MAX, workspace=ws,
+                                  accumulate=acc)
 
     for _ in range(max(args.warmup, 3)):
         out = step()
@@ -257,7 +262,7 @@ def run_gb300(args):
                       device=dev)
 
     def step_e2e():
-        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, l_max=L_MAX, workspace=wsh, out=outh)
+        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, l_max=L_MAX, workspace=wsh, out=outh, accumulate=acc)
 
     for _ in range(2):
         step_e2e()
@@ -311,6 +316,7 @@ def run_gb300(args):
                        "mean_iterations": float(iters.mean()), "max_iterations": int(iters.max()),
                        "fer": fails / (F * world), "undetected_errors": undetected,
                        "l2": "per-step decoder state ~2.8 GB > 129 MB L2 (no flush)",
+                       "accumulate": args.accumulate,
                        "parallelism": f"replicas x{world} (frames sharded, no collective on the path)"},
             "roofline": {"bound": "hbm", "kernel": "cn_kernel (check-node update, eq. 6)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",

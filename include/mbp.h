@@ -53,6 +53,23 @@ enum {
 /* message storage precision of the decoder */
 enum { MBP_MSG_F32 = 0, MBP_MSG_F64 = 1 };
 
+/*
+ * How the soft decision of eq. (2), L_V = L_P + sum of the node's C2V over all
+ * u matrices, is accumulated:
+ *  MBP_ACC_FLOAT  a second pass per iteration sums the node's messages in
+ *                 floating point, in stacked-row order (H_1's checks first);
+ *  MBP_ACC_FIXED  FP32 only: the check-node pass adds every message's change,
+ *                 rounded to a multiple of 2^-q, to a 32-bit integer sum per
+ *                 node, so each message is read once per iteration. q is the
+ *                 largest value <= 24 with (max node degree) x l_max x 2^q < 2^31
+ *                 (q = 22 for degree 16 and l_max 20); integer addition makes
+ *                 the result exact and independent of ordering. Needs q >= 12;
+ *  MBP_ACC_AUTO   (default) FLOAT. On GB300 the L2 reductions of FIXED cost
+ *                 more than the second read of the messages, so FIXED is an
+ *                 option, not the default.
+ */
+enum { MBP_ACC_AUTO = 0, MBP_ACC_FLOAT = 1, MBP_ACC_FIXED = 2 };
+
 /* One binary m x n matrix in compressed sparse rows, host memory, 0-based. */
 typedef struct {
   int32_t n, m, nnz;
@@ -78,6 +95,8 @@ typedef struct {
   void* soft_out;         /* optional device [F][n] posterior L_V of eq. (2) at the last iteration
                              each frame ran (float for F32, double for F64); NULL to skip */
   uint8_t* synd_ok;       /* optional device [F][u]: 1 where H_l x_hat = z^l for the output bits */
+  int32_t accumulate;     /* MBP_ACC_AUTO (default), MBP_ACC_FLOAT or MBP_ACC_FIXED */
+  int32_t reserved;
 } mbp_opts;
 
 /* Fill *opts with the defaults above (F32, early exit, l_max 20, no workspace). */
@@ -93,7 +112,8 @@ int mbp_version(void);
  * Upload u matrices H_1..H_u (Section 2: u > 1 matrices generated by PEG; u = 1
  * gives single-matrix BP). All must share n; m and nnz may differ. The library
  * copies the host arrays, validates them (MBP_EINVAL with *out = NULL on a
- * malformed matrix; MBP_EUNSUPPORTED for u > 16 or a check of degree > 64) and
+ * malformed matrix; MBP_EUNSUPPORTED for u > 16, a check of degree > 64 or a
+ * variable node with more than 64 edges over all u matrices) and
  * builds its device layouts on the current device. Synchronous.
  */
 int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out);

@@ -133,6 +133,8 @@ int validate_opts(const mbp_opts* o) {
   REQUIRE(o->msg_dtype == MBP_MSG_F32 || o->msg_dtype == MBP_MSG_F64, "unknown msg_dtype %d", o->msg_dtype);
   REQUIRE(o->early_exit == 0 || o->early_exit == 1, "early_exit must be 0 or 1");
   REQUIRE(std::isfinite(o->l_max) && o->l_max > 0, "l_max must be finite and > 0");
+  REQUIRE(o->accumulate == MBP_ACC_AUTO || o->accumulate == MBP_ACC_FLOAT || o->accumulate == MBP_ACC_FIXED,
+          "unknown accumulate mode %d", o->accumulate);
   return MBP_OK;
 }
 
@@ -259,6 +261,12 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   }
   std::vector<int32_t> col_ptr(n + 1, 0), col_slot(std::max<int64_t>(e_tot, 1));
   for (int64_t e = 0; e < e_tot; ++e) col_ptr[col_idx[e] + 1]++;
+  int32_t max_cdeg = 0;
+  for (int32_t i = 0; i < n; ++i) max_cdeg = std::max(max_cdeg, col_ptr[i + 1]);
+  if (max_cdeg > kMaxColDeg)
+    return set_error(MBP_EUNSUPPORTED, "a variable node has %d edges over all matrices; the limit is %d", max_cdeg,
+                     kMaxColDeg);
+  d.max_col_deg = max_cdeg;
   for (int32_t i = 0; i < n; ++i) col_ptr[i + 1] += col_ptr[i];
   {
     std::vector<int32_t> fill(col_ptr.begin(), col_ptr.end() - 1);
@@ -392,6 +400,7 @@ static int decode_common(const mbp_codes* codes, int F, const void* llr, const u
   a.z_bits = z_bits;
   a.max_iter = max_iter;
   a.early_exit = opts->early_exit;
+  a.accumulate = opts->accumulate;
   a.validate = opts->validate;
   a.l_max = opts->l_max;
   a.x_hat_bits = x_hat_bits;
@@ -448,6 +457,7 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   a.z_bits = st.io_z;
   a.max_iter = max_iter;
   a.early_exit = opts->early_exit;
+  a.accumulate = opts->accumulate;
   a.validate = opts->validate;
   a.l_max = opts->l_max;
   a.x_hat_bits = st.io_xhat;
@@ -500,6 +510,7 @@ int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits,
   a.z_bits = z_bits;
   a.max_iter = max_iter;
   a.early_exit = opts->early_exit;
+  a.accumulate = opts->accumulate;
   a.validate = 0;
   a.l_max = opts->l_max;
   a.x_hat_bits = x_hat_bits;

@@ -28,10 +28,14 @@ constexpr int kSliceRows = 4;   // rows per slice: one warp = kSliceRows rows x 
 constexpr int kMaxU = 16;
 constexpr int kMaxRowDeg = 64;
 constexpr int kMaxDevices = 64;
+constexpr int kMaxColDeg = 64;  // a variable node's edges over all u matrices
+constexpr int kMaxQBits = 24;   // fixed-point accumulation: at most 2^-24 resolution
+constexpr int kMinQBits = 12;   // and at least 2^-12
 
 struct DevCode {
   int32_t n, u, m_tot, n_slices;
   int32_t max_row_deg;
+  int32_t max_col_deg;
   int64_t e_tot, s_tot;
   int32_t m[kMaxU];
   int32_t row_first[kMaxU + 1];
@@ -51,6 +55,7 @@ struct DevState {
   void* c2v;          // [n_tiles][s_tot][kLanes] message type
   void* lv;           // [n_tiles][n][kLanes] posterior L_V of eq. (2)
   void* lp;           // [n_tiles][n][kLanes] channel LLR L_P
+  int32_t* lacc;      // [n_tiles][n][kLanes] fixed-point sum of C2V per node (FP32 single pass), or NULL
   uint8_t* xh;        // [n_tiles][n] hard decisions, bit lane
   uint8_t* zt;        // [n_tiles][m_tot] syndrome bits, bit lane
   uint32_t* active;   // [n_tiles] lanes still decoding
@@ -95,6 +100,7 @@ struct DecodeArgs {
   const uint32_t* z_bits;
   int max_iter;
   int early_exit;
+  int accumulate;
   int validate;
   double l_max;
   uint32_t* x_hat_bits;

@@ -19,6 +19,7 @@
 // where tanh rounds to 1 in FP32. The exclusion r != k uses prefix and suffix
 // (+)-combinations, never a division. Per edge this is two MUFU operations in,
 // two out (exp + reciprocal, reciprocal + log).
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
@@ -43,21 +44,39 @@ struct Arith<float> {
   static __device__ __forceinline__ float delta(float a) { return __fdividef(2.0f, 1.0f + __expf(a)); }
   // complement product a (+) b = a + b - a b
   static __device__ __forceinline__ float oplus(float p, float d) { return fmaf(d, 1.0f - p, p); }
-  // 2 atanh(1 - D) = ln((2 - D) / D), >= 0
-  static __device__ __forceinline__ float mag(float D) { return fmaxf(__logf(__fdividef(2.0f - D, D)), 0.0f); }
+  // 2 atanh(1 - D) = ln((2 - D) / D) for 0 <= D <= 1 (a value within rounding of 0 may come out as -0 or
+  // a tiny negative number; the caller ORs the message sign into the magnitude's sign bit)
+  static __device__ __forceinline__ float mag(float D) { return __logf(__fdividef(2.0f - D, D)); }
 };
 
 template <>
 struct Arith<double> {
   static __device__ __forceinline__ double delta(double a) { return 2.0 / (1.0 + exp(a)); }
   static __device__ __forceinline__ double oplus(double p, double d) { return fma(d, 1.0 - p, p); }
-  static __device__ __forceinline__ double mag(double D) { return fmax(log((2.0 - D) / D), 0.0); }
+  static __device__ __forceinline__ double mag(double D) { return log((2.0 - D) / D); }
 };
 
+constexpr uint32_t kSign = 0x80000000u;
+
+// Sign-bit access: sign_word returns a 32-bit word whose top bit is the sign.
 template <typename M>
-__device__ __forceinline__ M clampm(M v, M L) {
-  return v > L ? L : (v < -L ? -L : v);
-}
+struct Bits;
+
+template <>
+struct Bits<float> {
+  static __device__ __forceinline__ uint32_t sign_word(float x) { return __float_as_uint(x); }
+  static __device__ __forceinline__ float with_sign(float m, uint32_t sign) {
+    return __uint_as_float(__float_as_uint(m) | sign);
+  }
+};
+
+template <>
+struct Bits<double> {
+  static __device__ __forceinline__ uint32_t sign_word(double x) { return uint32_t(__double2hiint(x)); }
+  static __device__ __forceinline__ double with_sign(double m, uint32_t sign) {
+    return __hiloint2double(int(uint32_t(__double2hiint(m)) | sign), __double2loint(m));
+  }
+};
 
 // ------------------------------------------------------------- eq. (1)
 
@@ -173,10 +192,25 @@ __global__ void init_tiles_kernel(int F, int n_tiles, int u, uint32_t* __restric
 // ------------------------------------------------------------- eq. (6)
 
 // One warp per slice (kSliceRows rows x kLanes frames), 8 slices per block.
-template <typename M, int DMAX>
+// Every load of a row is issued before the first use: the slot columns, then
+// the posterior gathers and the old messages, so a warp waits for two memory
+// round trips per slice rather than two per edge.
+//
+// Signs travel in IEEE sign bits: the row's sign parity (with z_j) is the XOR
+// of the V2C words' top bits, and each edge's own sign is kept in the sign bit
+// of its delta, whose magnitude the (+) operations read through |.|.
+//
+// FIXED: also add each edge's change of message, q(C2V_new) - q(C2V_old) with
+// q(x) = round(x * qscale), to the posterior accumulator lacc of its variable
+// node (a 32-bit red.global.add in L2). Integer addition is associative, so
+// the accumulated sum sum_e q(C2V_e) is exact and independent of the order of
+// the atomics; finalize_kernel turns it into L_V. This removes the second read
+// of every message that vn_kernel needs.
+template <typename M, int DMAX, bool FIXED>
 __global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter, M* __restrict__ c2v,
                                                  const M* __restrict__ lsrc, const uint8_t* __restrict__ zt,
-                                                 const uint32_t* __restrict__ active, M l_max) {
+                                                 const uint32_t* __restrict__ active, M l_max,
+                                                 int32_t* __restrict__ lacc, float qscale) {
   const int tile = blockIdx.y;
   const uint32_t act = active[tile];
   if (act == 0) return;
@@ -187,53 +221,67 @@ __global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter
   const int r = s * kSliceRows + q;
   const int base = c.slice_base[s];
   const int deg = (c.slice_base[s + 1] - base) / kSliceRows;
-  const int64_t node0 = int64_t(tile) * c.n;
-  M* msg = c2v + int64_t(tile) * c.s_tot * kLanes;
+  const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
+  M* msg = c2v + (int64_t(tile) * c.s_tot + base + q) * kLanes + lane;  // edge k at msg[k * kSliceRows * kLanes]
+  const M* gsrc = lsrc + node0;                                         // node i at gsrc[i * kLanes]
+  const int* cols_p = c.slot_col + base + q;
+  const bool row_ok = r < c.m_tot;
+  const uint32_t zbyte = row_ok ? zt[int64_t(tile) * c.m_tot + r] : 0u;
 
-  M delta[DMAX], pre[DMAX];
-  uint64_t sgn = 0, valid = 0;
+  int col[DMAX];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(cols_p + k * kSliceRows) : -1;
+  M v[DMAX];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) v[k] = col[k] >= 0 ? __ldg(gsrc + col[k] * kLanes) : M(0);
+  [[maybe_unused]] M old[FIXED ? DMAX : 1];
+  if (!first_iter) {
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) {
+      const M o = col[k] >= 0 ? __ldcs(msg + k * kSliceRows * kLanes) : M(0);
+      if constexpr (FIXED) old[k] = o;
+      v[k] -= o;
+    }
+  } else if constexpr (FIXED) {
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) old[k] = M(0);
+  }
+  uint32_t par = ((zbyte >> lane) & 1u) << 31;
+  M pre[DMAX];
   M P = M(0);
 #pragma unroll
   for (int k = 0; k < DMAX; ++k) {
-    if (k < deg) {
-      const int slot = base + k * kSliceRows + q;
-      const int col = __ldg(c.slot_col + slot);
-      M d = M(0);
-      if (col >= 0) {
-        M v = __ldg(lsrc + (node0 + col) * kLanes + lane);
-        if (!first_iter) v -= msg[int64_t(slot) * kLanes + lane];
-        v = clampm(v, l_max);
-        sgn |= uint64_t(v < M(0)) << k;
-        valid |= uint64_t(1) << k;
-        d = Arith<M>::delta(fabs(v));
-      }
-      delta[k] = d;
-      pre[k] = P;
-      P = Arith<M>::oplus(P, d);
-    }
+    const uint32_t sx = Bits<M>::sign_word(v[k]);
+    par ^= sx;
+    const M d = col[k] >= 0 ? Arith<M>::delta(fmin(fabs(v[k]), l_max)) : M(0);
+    v[k] = Bits<M>::with_sign(d, sx & kSign);
+    pre[k] = P;
+    P = Arith<M>::oplus(P, d);
   }
-  if (r >= c.m_tot || !((act >> lane) & 1u)) return;
-  const uint32_t z = (zt[int64_t(tile) * c.m_tot + r] >> lane) & 1u;
-  const uint32_t par = (__popcll(sgn) & 1u) ^ z;
+  if (!row_ok || !((act >> lane) & 1u)) return;
   M S = M(0);
 #pragma unroll
   for (int k = DMAX - 1; k >= 0; --k) {
-    if (k < deg) {
-      if ((valid >> k) & 1u) {
-        const M D = Arith<M>::oplus(pre[k], S);
-        const M mag = fmin(Arith<M>::mag(D), l_max);
-        const uint32_t sk = par ^ uint32_t((sgn >> k) & 1u);
-        msg[int64_t(base + k * kSliceRows + q) * kLanes + lane] = sk ? -mag : mag;
+    if (col[k] >= 0) {
+      const M D = Arith<M>::oplus(pre[k], S);
+      const M mag = fmin(Arith<M>::mag(D), l_max);
+      const M nv = Bits<M>::with_sign(mag, (par ^ Bits<M>::sign_word(v[k])) & kSign);
+      __stcs(msg + k * kSliceRows * kLanes, nv);
+      if constexpr (FIXED) {
+        const int32_t dq = __float2int_rn(float(nv) * qscale) - __float2int_rn(float(old[k]) * qscale);
+        if (dq != 0) atomicAdd(lacc + node0 + col[k] * kLanes, dq);
       }
-      S = Arith<M>::oplus(S, delta[k]);
     }
+    S = Arith<M>::oplus(S, fabs(v[k]));
   }
 }
 
 // ------------------------------------------------------------- eq. (2)
 
-// Block: 32 variable nodes x 8 lanes. Sums in stacked-row order.
-template <typename M>
+// Block: 32 variable nodes x 8 lanes. Sums in stacked-row order; the slot
+// indices of a node are loaded before the message gathers, so the gathers of
+// one node are in flight together. DMAX bounds the node degree (all matrices).
+template <typename M, int DMAX>
 __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __restrict__ c2v, M* __restrict__ lv,
                                                  const M* __restrict__ lp, uint8_t* __restrict__ xh,
                                                  const uint32_t* __restrict__ active) {
@@ -244,12 +292,48 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __res
   const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
   const bool ok = col < c.n;
   const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
-  const M* msg = c2v + int64_t(tile) * c.s_tot * kLanes;
+  const M* msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
   M sum = M(0);
   if (ok) {
+    const int a0 = c.col_ptr[col];
+    const int d = c.col_ptr[col + 1] - a0;
+    int slot[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) slot[k] = k < d ? __ldg(c.col_slot + a0 + k) : -1;
+    M g[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) g[k] = slot[k] >= 0 ? __ldcs(msg + int64_t(slot[k]) * kLanes) : M(0);
     sum = lp[at];
-    const int a1 = c.col_ptr[col + 1];
-    for (int a = c.col_ptr[col]; a < a1; ++a) sum += msg[int64_t(__ldg(c.col_slot + a)) * kLanes + lane];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (slot[k] >= 0) sum += g[k];
+    if ((act >> lane) & 1u) lv[at] = sum;
+  }
+  const uint32_t b = __ballot_sync(kFull, ok && sum < M(0));
+  if (ok && lane == 0) {
+    const uint32_t nb = (b >> (threadIdx.x & 24)) & 0xffu;
+    uint8_t* px = xh + int64_t(tile) * c.n + col;
+    *px = uint8_t((*px & ~act) | (nb & act));
+  }
+}
+
+// L_V = L_P + lacc / qscale and the hard decision, for the fixed-point single
+// pass. Block: 32 variable nodes x 8 lanes.
+template <typename M>
+__global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const int32_t* __restrict__ lacc,
+                                                       M* __restrict__ lv, const M* __restrict__ lp,
+                                                       uint8_t* __restrict__ xh, const uint32_t* __restrict__ active,
+                                                       float inv_qscale) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int lane = threadIdx.x & 7;
+  const int col = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const bool ok = col < c.n;
+  const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
+  M sum = M(0);
+  if (ok) {
+    sum = lp[at] + M(float(lacc[at]) * inv_qscale);
     if ((act >> lane) & 1u) lv[at] = sum;
   }
   const uint32_t b = __ballot_sync(kFull, ok && sum < M(0));
@@ -263,6 +347,9 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __res
 // ------------------------------------------------------- stopping rule
 
 // One thread per (tile, stacked row): lanes whose hard decision breaks the row.
+// The row's columns come from the slot layout and are all loaded before the
+// decision bytes are gathered.
+template <int DMAX>
 __global__ void __launch_bounds__(256) syn_kernel(const DevCode c, const uint8_t* __restrict__ xh,
                                                   const uint8_t* __restrict__ zt,
                                                   const uint32_t* __restrict__ active, uint32_t* __restrict__ fail) {
@@ -273,10 +360,18 @@ __global__ void __launch_bounds__(256) syn_kernel(const DevCode c, const uint8_t
   uint32_t bad = 0;
   int l = -1;
   if (r < c.m_tot) {
+    const int s = r / kSliceRows, q = r % kSliceRows;
+    const int base = c.slice_base[s];
+    const int deg = (c.slice_base[s + 1] - base) / kSliceRows;
+    const int* cp = c.slot_col + base + q;
+    int col[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(cp + k * kSliceRows) : -1;
     const uint8_t* x = xh + int64_t(tile) * c.n;
     uint32_t p = zt[int64_t(tile) * c.m_tot + r];
-    const int e1 = c.row_ptr[r + 1];
-    for (int e = c.row_ptr[r]; e < e1; ++e) p ^= x[__ldg(c.col_idx + e)];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (col[k] >= 0) p ^= x[col[k]];
     bad = p & act;
     l = c.row_mat[r];
   }
@@ -359,20 +454,35 @@ __global__ void export_c2v_kernel(const DevCode c, const M* __restrict__ c2v, in
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
-template <typename M, int DMAX>
-void launch_cn(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s) {
+template <typename M, int DMAX, bool FIXED>
+void launch_cn(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale, cudaStream_t s) {
   dim3 grid(blocks_for(c.n_slices, 8), st.n_tiles);
-  cn_kernel<M, DMAX><<<grid, 256, 0, s>>>(c, first_iter, static_cast<M*>(st.c2v),
-                                          static_cast<const M*>(first_iter ? st.lp : st.lv), st.zt, st.active,
-                                          M(l_max));
+  cn_kernel<M, DMAX, FIXED><<<grid, 256, 0, s>>>(c, first_iter, static_cast<M*>(st.c2v),
+                                                 static_cast<const M*>(first_iter ? st.lp : st.lv), st.zt, st.active,
+                                                 M(l_max), st.lacc, qscale);
+}
+
+template <typename M, bool FIXED>
+void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale,
+                   cudaStream_t s) {
+  if (c.max_row_deg <= 8) launch_cn<M, 8, FIXED>(c, st, first_iter, l_max, qscale, s);
+  else if (c.max_row_deg <= 16) launch_cn<M, 16, FIXED>(c, st, first_iter, l_max, qscale, s);
+  else if (c.max_row_deg <= 32) launch_cn<M, 32, FIXED>(c, st, first_iter, l_max, qscale, s);
+  else launch_cn<M, 64, FIXED>(c, st, first_iter, l_max, qscale, s);
+}
+
+template <typename M, int DMAX>
+void launch_vn(const DevCode& c, const DevState& st, cudaStream_t s) {
+  vn_kernel<M, DMAX><<<dim3(blocks_for(c.n, 32), st.n_tiles), 256, 0, s>>>(
+      c, static_cast<const M*>(st.c2v), static_cast<M*>(st.lv), static_cast<const M*>(st.lp), st.xh, st.active);
 }
 
 template <typename M>
-void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s) {
-  if (c.max_row_deg <= 8) launch_cn<M, 8>(c, st, first_iter, l_max, s);
-  else if (c.max_row_deg <= 16) launch_cn<M, 16>(c, st, first_iter, l_max, s);
-  else if (c.max_row_deg <= 32) launch_cn<M, 32>(c, st, first_iter, l_max, s);
-  else launch_cn<M, 64>(c, st, first_iter, l_max, s);
+void launch_vn_any(const DevCode& c, const DevState& st, cudaStream_t s) {
+  if (c.max_col_deg <= 8) launch_vn<M, 8>(c, st, s);
+  else if (c.max_col_deg <= 16) launch_vn<M, 16>(c, st, s);
+  else if (c.max_col_deg <= 32) launch_vn<M, 32>(c, st, s);
+  else launch_vn<M, kMaxColDeg>(c, st, s);
 }
 
 template <typename M>
@@ -382,7 +492,20 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
   if ((e = (call)) != cudaSuccess) return cuda_error(e, what)
 #define CKL(what) CK(cudaGetLastError(), what)
   const int F = st.F, NT = st.n_tiles;
+  // accumulation of eq. (2): fixed-point single pass (FP32 messages) or float two-pass
+  int qbits = 0;
+  {
+    const double bound = double(c.max_col_deg > 0 ? c.max_col_deg : 1) * a.l_max;
+    while (qbits < kMaxQBits && bound * std::ldexp(1.0, qbits + 1) < 2147483647.0) ++qbits;
+  }
+  const bool fixed_ok = sizeof(M) == 4 && st.lacc && qbits >= kMinQBits;
+  if (a.accumulate == MBP_ACC_FIXED && !fixed_ok)
+    return set_error(MBP_EUNSUPPORTED, "fixed-point accumulation needs FP32 messages and max node degree x l_max"
+                                       " <= 2^%d", 31 - kMinQBits);
+  const bool fixed = fixed_ok && a.accumulate == MBP_ACC_FIXED;
+  const float qscale = float(std::ldexp(1.0, qbits)), inv_qscale = float(std::ldexp(1.0, -qbits));
   CK(cudaMemsetAsync(st.counters, 0, 4 * sizeof(int32_t), s), "clear counters");
+  if (fixed) CK(cudaMemsetAsync(st.lacc, 0, size_t(NT) * c.n * kLanes * sizeof(int32_t), s), "clear accumulator");
   prof_begin(MBP_KERNEL_SETUP, s);
   if (a.y_bits) {
     frame_mag_kernel<<<blocks_for(F, 256), 256, 0, s>>>(a.qber, F, st.llr_mag);
@@ -406,7 +529,10 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
   const dim3 syn_grid(blocks_for(c.m_tot, 256), NT);
   auto stop_check = [&](int t, int* left) -> int {
     prof_begin(MBP_KERNEL_SYNDROME, s);
-    syn_kernel<<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    if (c.max_row_deg <= 8) syn_kernel<8><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    else if (c.max_row_deg <= 16) syn_kernel<16><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    else if (c.max_row_deg <= 32) syn_kernel<32><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    else syn_kernel<kMaxRowDeg><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
     CKL("syn_kernel");
     prof_end(MBP_KERNEL_SYNDROME, s, 1);
     CK(cudaMemsetAsync(st.counters, 0, sizeof(int32_t), s), "clear counter");
@@ -427,13 +553,20 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
   }
   for (int t = 1; t <= a.max_iter && left > 0; ++t) {
     prof_begin(MBP_KERNEL_CHECK, s);
-    launch_cn_any<M>(c, st, t == 1, a.l_max, s);
+    if constexpr (sizeof(M) == 4) {
+      if (fixed) launch_cn_any<M, true>(c, st, t == 1, a.l_max, qscale, s);
+      else launch_cn_any<M, false>(c, st, t == 1, a.l_max, qscale, s);
+    } else {
+      launch_cn_any<M, false>(c, st, t == 1, a.l_max, qscale, s);
+    }
     CKL("cn_kernel");
     prof_end(MBP_KERNEL_CHECK, s, 1);
     prof_begin(MBP_KERNEL_VARIABLE, s);
-    vn_kernel<M><<<dim3(blocks_for(c.n, 32), NT), 256, 0, s>>>(c, static_cast<const M*>(st.c2v),
-                                                               static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
-                                                               st.xh, st.active);
+    if (fixed)
+      finalize_kernel<M><<<dim3(blocks_for(c.n, 32), NT), 256, 0, s>>>(
+          c, st.lacc, static_cast<M*>(st.lv), static_cast<const M*>(st.lp), st.xh, st.active, inv_qscale);
+    else
+      launch_vn_any<M>(c, st, s);
     CKL("vn_kernel");
     prof_end(MBP_KERNEL_VARIABLE, s, 1);
     if (a.early_exit || t == a.max_iter) {
@@ -480,6 +613,8 @@ cudaError_t launch_bsc_llr(const uint32_t* y_bits, const double* qber, int F, in
 
 static size_t msg_size(int msg_dtype) { return msg_dtype == MBP_MSG_F64 ? 8 : 4; }
 
+constexpr int kRegions = 16;
+
 static void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, size_t* total) {
   const size_t NT = (size_t(F) + kLanes - 1) / kLanes;
   const size_t ms = msg_size(msg_dtype);
@@ -490,6 +625,7 @@ static void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t*
       NT * size_t(c.s_tot) * kLanes * ms,  // c2v
       NT * size_t(c.n) * kLanes * ms,      // lv
       NT * size_t(c.n) * kLanes * ms,      // lp
+      msg_dtype == MBP_MSG_F32 ? NT * size_t(c.n) * kLanes * 4 : 0,  // lacc
       NT * size_t(c.n),                    // xh
       NT * size_t(c.m_tot),                // zt
       NT * 4,                              // active
@@ -504,7 +640,7 @@ static void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t*
       host_io ? size_t(F) : 0,             // io_success
   };
   size_t t = 0;
-  for (int i = 0; i < 15; ++i) {
+  for (int i = 0; i < kRegions; ++i) {
     offs[i] = t;
     t += align256(sizes[i]);
   }
@@ -512,13 +648,13 @@ static void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t*
 }
 
 size_t workspace_bytes(const DevCode& c, int F, int msg_dtype, bool host_io) {
-  size_t offs[15], total;
+  size_t offs[kRegions], total;
   layout(c, F, msg_dtype, host_io, offs, &total);
   return total;
 }
 
 void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void* base, DevState* st) {
-  size_t o[15], total;
+  size_t o[kRegions], total;
   layout(c, F, msg_dtype, host_io, o, &total);
   char* b = static_cast<char*>(base);
   st->F = F;
@@ -526,18 +662,19 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->c2v = b + o[0];
   st->lv = b + o[1];
   st->lp = b + o[2];
-  st->xh = reinterpret_cast<uint8_t*>(b + o[3]);
-  st->zt = reinterpret_cast<uint8_t*>(b + o[4]);
-  st->active = reinterpret_cast<uint32_t*>(b + o[5]);
-  st->fail = reinterpret_cast<uint32_t*>(b + o[6]);
-  st->llr_mag = reinterpret_cast<double*>(b + o[7]);
-  st->counters = reinterpret_cast<int32_t*>(b + o[8]);
-  st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[9]) : nullptr;
-  st->io_qber = host_io ? reinterpret_cast<double*>(b + o[10]) : nullptr;
-  st->io_z = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;
-  st->io_xhat = host_io ? reinterpret_cast<uint32_t*>(b + o[12]) : nullptr;
-  st->io_iters = host_io ? reinterpret_cast<int32_t*>(b + o[13]) : nullptr;
-  st->io_success = host_io ? reinterpret_cast<uint8_t*>(b + o[14]) : nullptr;
+  st->lacc = msg_dtype == MBP_MSG_F32 ? reinterpret_cast<int32_t*>(b + o[3]) : nullptr;
+  st->xh = reinterpret_cast<uint8_t*>(b + o[4]);
+  st->zt = reinterpret_cast<uint8_t*>(b + o[5]);
+  st->active = reinterpret_cast<uint32_t*>(b + o[6]);
+  st->fail = reinterpret_cast<uint32_t*>(b + o[7]);
+  st->llr_mag = reinterpret_cast<double*>(b + o[8]);
+  st->counters = reinterpret_cast<int32_t*>(b + o[9]);
+  st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[10]) : nullptr;
+  st->io_qber = host_io ? reinterpret_cast<double*>(b + o[11]) : nullptr;
+  st->io_z = host_io ? reinterpret_cast<uint32_t*>(b + o[12]) : nullptr;
+  st->io_xhat = host_io ? reinterpret_cast<uint32_t*>(b + o[13]) : nullptr;
+  st->io_iters = host_io ? reinterpret_cast<int32_t*>(b + o[14]) : nullptr;
+  st->io_success = host_io ? reinterpret_cast<uint8_t*>(b + o[15]) : nullptr;
 }
 
 int decode(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {

@@ -100,36 +100,50 @@ def test_bsc_llr_matches_oracle(mbp):
 
 # ------------------------------------------------------- whole decoder
 
-def _decode_both(mbp, w, max_iter, msg64, early_exit=True, want_lv=False, threads=8):
+MODES = ["f64", "f32-float", "f32-fixed"]
+
+
+def mode_args(mbp, mode):
+    if mode == "f64":
+        return dict(msg_dtype=mbp.MSG_F64, accumulate=mbp.ACC_FLOAT)
+    if mode == "f32-float":
+        return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FLOAT)
+    return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FIXED)
+
+
+def _decode_both(mbp, w, max_iter, msg64, early_exit=True, want_lv=False, threads=8, mode=None):
     codes = mbp.mbp_create_codes(w.H)
     z = gpu_syndrome(mbp, codes, w.x)
     y = dev(u32_to_i32(w.y))
     e = dev(w.e)
-    out = mbp.mbp_decode_bsc(codes, y, e, z, max_iter, msg_dtype=mbp.MSG_F64 if msg64 else mbp.MSG_F32,
-                             early_exit=early_exit, want_soft=want_lv, want_synd=True)
+    kw = mode_args(mbp, mode) if mode else dict(msg_dtype=mbp.MSG_F64 if msg64 else mbp.MSG_F32)
+    out = mbp.mbp_decode_bsc(codes, y, e, z, max_iter, early_exit=early_exit, want_soft=want_lv, want_synd=True,
+                             **kw)
     torch.cuda.synchronize()
     ref = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, max_iter, early_exit=early_exit, threads=threads,
                      want_lv=want_lv, want_synd=True)
     return codes, out, ref
 
 
-@pytest.mark.parametrize("msg64", [True, False])
-def test_rate05_n1024_u2_qber3(mbp, msg64):
+@pytest.mark.parametrize("mode", MODES)
+def test_rate05_n1024_u2_qber3(mbp, mode):
     """n=1024, m=512 per matrix, d_v=3, u=2, QBER 3%, 64 frames, max 50 iterations, seed 0."""
+    msg64 = mode == "f64"
     w = Workload(1024, 512, {3: 1.0}, 2, 0, 64, 0.03)
-    _, out, ref = _decode_both(mbp, w, 50, msg64, want_lv=True)
+    _, out, ref = _decode_both(mbp, w, 50, msg64, want_lv=True, mode=mode)
     check_outputs_bit_exact(out, ref, w.n, fp64=msg64)
     assert ref["success"].all()
-    if msg64:
-        assert np.allclose(out["soft"].cpu().numpy(), ref["L_V"], atol=TOL_F64)
+    tol = TOL_F64 if msg64 else TOL_F32
+    assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= tol
 
 
-@pytest.mark.parametrize("msg64", [True, False])
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("t", [1, 2, 3, 4, 5])
-def test_messages_within_tolerance_first_iterations(mbp, msg64, t):
+def test_messages_within_tolerance_first_iterations(mbp, mode, t):
     """C2V and L_V after t flooding iterations (no early exit), 13 frames = 2 tiles with a ragged tail."""
+    msg64 = mode == "f64"
     w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 13, 0.05)
-    codes, out, ref = _decode_both(mbp, w, t, msg64, early_exit=False, want_lv=True)
+    codes, out, ref = _decode_both(mbp, w, t, msg64, early_exit=False, want_lv=True, mode=mode)
     tol = TOL_F64 if msg64 else TOL_F32
     ref_c2v = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, t, early_exit=False, want_c2v=True)["c2v"]
     assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= tol
@@ -139,14 +153,16 @@ def test_messages_within_tolerance_first_iterations(mbp, msg64, t):
     assert np.array_equal(out["iters"].cpu().numpy(), np.full(w.F, t))
 
 
-def test_rate07_n65536_first_iterations_fp32(mbp):
+@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed"])
+def test_rate07_n65536_first_iterations_fp32(mbp, mode):
     """The n=65536 rate-0.7 code: FP32 C2V/L_V within 1e-3 of the oracle over iterations 1..5."""
     w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 3, 0.02)
     LP = orc.bsc_llr(w.y, w.n, w.e)
     codes = mbp.mbp_create_codes(w.H)
     z = gpu_syndrome(mbp, codes, w.x)
     for t in range(1, 6):
-        out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y)), dev(w.e), z, t, early_exit=False, want_soft=True)
+        out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y)), dev(w.e), z, t, early_exit=False, want_soft=True,
+                                 **mode_args(mbp, mode))
         ref = orc.decode(w.H, LP, w.z_orc, t, early_exit=False, want_lv=True, want_c2v=True, threads=3)
         assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= TOL_F32
         for f in range(w.F):
@@ -154,10 +170,11 @@ def test_rate07_n65536_first_iterations_fp32(mbp):
             assert np.max(np.abs(c - ref["c2v"][f])) <= TOL_F32
 
 
-def test_rate07_n65536_subset_bit_exact(mbp):
+@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed"])
+def test_rate07_n65536_subset_bit_exact(mbp, mode):
     """n=65536, R=0.7, d_v {2,3,8}, u=2, QBER 2%: 64 frames, max 60 iterations."""
     w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 64, 0.02)
-    _, out, ref = _decode_both(mbp, w, 60, False)
+    _, out, ref = _decode_both(mbp, w, 60, False, mode=mode)
     mism = check_outputs_bit_exact(out, ref, w.n)
     assert ref["success"].all() and mism <= 1
     assert np.array_equal(host_u32(out["x_hat_bits"]), w.x)
@@ -298,6 +315,12 @@ def test_invalid_arguments_return_errors(mbp):
     rc = lib.mbp_decode_batch(codes.handle, 8, llr.data_ptr(), z.data_ptr(), 10, ctypes.byref(o), xh.data_ptr(),
                               host.ctypes.data, ok.data_ptr(), None)
     assert rc == 1 and b"iters" in lib.mbp_last_error_string()
+    o.l_max = 20.0
+    o.accumulate = 7
+    rc = lib.mbp_decode_batch(codes.handle, 8, llr.data_ptr(), z.data_ptr(), 10, ctypes.byref(o), xh.data_ptr(),
+                              it.data_ptr(), ok.data_ptr(), None)
+    assert rc == 1
+    o.accumulate = 0
     o.l_max = -1.0
     rc = lib.mbp_decode_batch(codes.handle, 8, llr.data_ptr(), z.data_ptr(), 10, ctypes.byref(o), xh.data_ptr(),
                               it.data_ptr(), ok.data_ptr(), None)
@@ -313,3 +336,26 @@ def test_workspace_reuse_across_calls(mbp):
     b = mbp.mbp_decode_bsc(codes, y, e, z, 30, workspace=a["workspace"])
     for k in ("x_hat_bits", "iters", "success"):
         assert torch.equal(a[k], b[k])
+
+
+def test_fixed_accumulation_refused_for_fp64(mbp):
+    w = Workload(512, 200, {3: 1.0}, 2, 3, 8, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    with pytest.raises(mbp.MBPError) as ei:
+        mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y)), dev(w.e), z, 10, msg_dtype=mbp.MSG_F64,
+                           accumulate=mbp.ACC_FIXED)
+    assert ei.value.status == 5
+
+
+def test_accumulation_modes_agree(mbp):
+    """Both FP32 accumulations decode the same frames to the same bits at QBER 5% on a mid-size code."""
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 40, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y, e = dev(u32_to_i32(w.y)), dev(w.e)
+    a = mbp.mbp_decode_bsc(codes, y, e, z, 40, accumulate=mbp.ACC_FLOAT)
+    b = mbp.mbp_decode_bsc(codes, y, e, z, 40, accumulate=mbp.ACC_FIXED)
+    ok = (a["success"] == 1) & (b["success"] == 1)
+    assert torch.equal(a["x_hat_bits"][ok], b["x_hat_bits"][ok])
+    assert int(ok.sum()) >= 35
