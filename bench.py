@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--accumulate", default="auto", choices=["auto", "float", "fixed"],
                    help="eq. (2) accumulation: fixed-point single pass or float second pass")
+    p.add_argument("--schedule", default="auto", choices=["auto", "streaming", "resident"],
+                   help="kernels per iteration, or one cooperative launch keeping tile groups in L2")
     return p.parse_args()
 
 
@@ -69,10 +71,20 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(n, e_tot, msg_bytes=4):
-    """Per frame-iteration: the check kernel's floor (messages read + written once, posterior read once)
-    and the whole iteration's floor 2 s E + 12 n (posterior read, written and gathered once)."""
-    return 2 * msg_bytes * e_tot + 4 * n, 2 * msg_bytes * e_tot + 12 * n
+def algorithmic_bytes(iters, n, e_tot, msg_bytes=4):
+    """Floor bytes of the frame-iterations run, for the check kernel and for the whole path.
+
+    Every iteration writes each message once and reads the posterior once (check
+    kernel: s E + 4 n); every iteration after a frame's first also reads the
+    previous messages (s E). The whole path adds writing and re-reading the
+    posterior (8 n): 2 s E + 12 n per iteration after the first.
+    """
+    it = np.asarray(iters, dtype=np.int64)
+    later = np.maximum(it - 1, 0)
+    sE = msg_bytes * e_tot
+    check = int(np.sum(it * (sE + 4 * n) + later * sE))
+    path = int(np.sum(it * (sE + 12 * n) + later * sE))
+    return check, path
 
 
 class ClockSampler:
@@ -121,6 +133,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_inputs(frames, rank):
+    """Weak scaling: every rank reconciles its own `frames` frames (frame stream = rank)."""
+    return mi.bsc_frames(N, frames, QBER, seed=SEED, stream=rank)
+
+
+def reduce_over_ranks(dist, device, ms, ms_e2e, fails, undetected):
+    """Slowest rank's times (MAX) and the job's failure counts (SUM); identity for one process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, ms_e2e, fails, undetected
+    import torch
+    t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([fails, undetected], dtype=torch.int64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(c[0]), int(c[1])
+
+
+def job_mbps(frames_per_rank, world, ms):
+    """Whole-job throughput: bits of every rank's frames over the slowest rank's time."""
+    return frames_per_rank * N * world / (ms / 1e3) / 1e6
+
+
 def cpu_count():
     try:
         return len(os.sched_getaffinity(0))
@@ -138,18 +172,23 @@ def oracle_time(H, x, y, e, frames, threads):
     return dt, out
 
 
-def kernel_traffic(mean_frames_per_launch):
-    """DRAM bytes per check-kernel launch from the committed ncu summary, if it was taken on this source."""
-    path = os.path.join(ROOT, "profiles", "check_node_kernel_n65536.txt")
+def kernel_traffic(iters, launches, summary):
+    """Mean DRAM bytes per launch of the dominant kernel, from the committed full-size ncu capture (bytes per
+    frame in a frame's first iteration and in a later one), if that capture was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2001_07979_gb300", "csrc", "mbp_kernels.cu")
     try:
         text = open(path).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         kv = dict(line.split("=", 1) for line in text.splitlines() if "=" in line and not line.startswith("#"))
         kv = {k.strip(): v.strip() for k, v in kv.items()}
-        if kv.get("kernel_source_sha256_16") != digest:
+        if kv.get("kernel_source_sha256_16") != digest or not launches:
             return None
-        return float(kv["dram_bytes_per_frame_iteration"]) * mean_frames_per_launch
+        it = np.asarray(iters, dtype=np.int64)
+        first, later = int(np.sum(it >= 1)), int(np.sum(np.maximum(it - 1, 0)))
+        total = first * float(kv["dram_bytes_per_frame_first_iteration"]) + \
+            later * float(kv["dram_bytes_per_frame_later_iteration"])
+        return total / launches
     except Exception:
         return None
 
@@ -204,7 +243,7 @@ def run_gb300(args):
 
     F = args.frames
     H = mi.make_codes(N, M, DIST, U, SEED)
-    x, y, e = mi.bsc_frames(N, F, QBER, seed=SEED, stream=rank)
+    x, y, e = rank_inputs(F, rank)
     codes = mbp.mbp_create_codes(H)
     dev = torch.device("cuda", local)
     xd = torch.from_numpy(x.view(np.int32)).to(dev)
@@ -215,10 +254,11 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
 
     acc = {"auto": mbp.ACC_AUTO, "float": mbp.ACC_FLOAT, "fixed": mbp.ACC_FIXED}[args.accumulate]
+    sched = {"auto": mbp.SCHED_AUTO, "streaming": mbp.SCHED_STREAMING, "resident": mbp.SCHED_RESIDENT}[args.schedule]
 
     def step():
         return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=mbp.MSG_F32, l_max=L_MAX, workspace=ws,
-                                  accumulate=acc)
+                                  accumulate=acc, schedule=sched)
 
     for _ in range(max(args.warmup, 3)):
         out = step()
@@ -262,7 +302,8 @@ def run_gb300(args):
                       device=dev)
 
     def step_e2e():
-        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, l_max=L_MAX, workspace=wsh, out=outh, accumulate=acc)
+        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, l_max=L_MAX, workspace=wsh, out=outh, accumulate=acc,
+                                schedule=sched)
 
     for _ in range(2):
         step_e2e()
@@ -280,30 +321,30 @@ def run_gb300(args):
     h2d = yh.numel() * 4 + eh.numel() * 8 + zh.numel() * 4
     d2h = outh["x_hat_bits"].numel() * 4 + F * 4 + F
 
-    if world > 1:
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
-        fails_t = torch.tensor([fails, undetected], dtype=torch.int64, device=dev)
-        dist.all_reduce(fails_t)
-        fails, undetected = int(fails_t[0]), int(fails_t[1])
-
-    bits = F * N * world
-    value = bits / (ms / 1e3) / 1e6
-    value_e2e = bits / (ms_e2e / 1e3) / 1e6
+    ms, ms_e2e, fails, undetected = reduce_over_ranks(dist if world > 1 else None, dev, ms, ms_e2e, fails,
+                                                      undetected)
+    value = job_mbps(F, world, ms)
+    value_e2e = job_mbps(F, world, ms_e2e)
 
     # roofline of the dominant kernel: algorithmic bytes of the frame-iterations it ran / its event time
     e_tot = codes.edges
-    b_check, b_iter = algorithmic_bytes(N, e_tot)
-    frame_iters = int(iters.sum()) * args.steps
-    n_check, ms_check = prof["check"]
+    b_check, b_path = algorithmic_bytes(iters, N, e_tot)  # one step
     peak, peak_src = load_peaks()
-    achieved = b_check * frame_iters / (ms_check / 1e3) / 1e9 if ms_check > 0 else None
-    mean_frames = frame_iters / n_check if n_check else 0
-    traffic = kernel_traffic(mean_frames)
     dominant = max(prof, key=lambda k: prof[k][1])
     launches = int(sum(v[0] for v in prof.values()))
-    path_gbs = b_iter * frame_iters / (ms * args.steps / 1e3) / 1e9
+    path_gbs = b_path / (ms / 1e3) / 1e9
+    if dominant == "persistent":
+        # one cooperative launch runs every step of every iteration: its algorithmic bytes are the path's
+        n_dom, ms_dom = prof["persistent"]
+        kernel_name = "resident_kernel (all steps of eq. 6, eq. 2 and the stopping rule, tile groups in L2)"
+        b_dom, rule = b_path, "2*s*E+12n per frame-iteration (s*E less in a frame's first)"
+        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "resident_kernel_n65536.txt")
+    else:
+        n_dom, ms_dom = prof["check"]
+        kernel_name = "cn_kernel (check-node update, eq. 6)"
+        b_dom, rule = b_check, "per frame: s*E+4n per iteration, plus s*E per iteration after the first"
+        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "check_node_kernel_n65536.txt")
+    achieved = b_dom * args.steps / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
 
     result = None
     if rank == 0:
@@ -316,16 +357,18 @@ def run_gb300(args):
                        "mean_iterations": float(iters.mean()), "max_iterations": int(iters.max()),
                        "fer": fails / (F * world), "undetected_errors": undetected,
                        "l2": "per-step decoder state ~2.8 GB > 129 MB L2 (no flush)",
-                       "accumulate": args.accumulate,
+                       "accumulate": args.accumulate, "schedule": args.schedule,
                        "parallelism": f"replicas x{world} (frames sharded, no collective on the path)"},
-            "roofline": {"bound": "hbm", "kernel": "cn_kernel (check-node update, eq. 6)",
+            "roofline": {"bound": "hbm", "kernel": kernel_name,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_source": f"{peak_src} HBM copy bandwidth",
-                         "bytes_per_frame_iteration": b_check, "launches": n_check,
-                         "mean_launch_ms": ms_check / n_check if n_check else None,
+                         "algorithmic_bytes_per_step": b_dom, "bytes_rule": rule,
+                         "launches": n_dom,
+                         "mean_launch_ms": ms_dom / n_dom if n_dom else None,
                          "dominant_family": dominant,
-                         "path_gbs_at_2sE_plus_12n": path_gbs, "path_frac": path_gbs / peak},
+                         "path_gbs": path_gbs, "path_frac": path_gbs / peak,
+                         "path_bytes_rule": "2*s*E+12n per frame-iteration (s*E less in a frame's first)"},
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()},
             "gpu_launches": launches,
             "clocks": clk,

@@ -46,7 +46,7 @@ enum {
   MBP_EINVAL = 1,       /* invalid argument: null pointer, bad size, malformed matrix, non-finite LLR */
   MBP_ENOMEM = 2,       /* host or device allocation inside mbp_create_codes failed */
   MBP_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
-  MBP_ETIMEOUT = 4,     /* reserved: a bounded device-side wait gave up */
+  MBP_ETIMEOUT = 4,     /* a bounded device-side wait (grid barrier of the resident schedule) gave up */
   MBP_EUNSUPPORTED = 5  /* valid input outside this build's limits (e.g. a check of degree > 64) */
 };
 
@@ -69,6 +69,23 @@ enum { MBP_MSG_F32 = 0, MBP_MSG_F64 = 1 };
  *                 option, not the default.
  */
 enum { MBP_ACC_AUTO = 0, MBP_ACC_FLOAT = 1, MBP_ACC_FIXED = 2 };
+
+/*
+ * How the iterations are scheduled on the GPU (results are the same):
+ *  MBP_SCHED_STREAMING  one kernel per step (check nodes, variable nodes,
+ *                       syndrome test, retirement) per iteration over every
+ *                       tile of 8 frames that is still decoding; messages
+ *                       stream through HBM each iteration;
+ *  MBP_SCHED_RESIDENT   one cooperative launch that takes the tiles a group at
+ *                       a time, as many as keep the group's messages within
+ *                       3/4 of L2, and runs all of a group's iterations with
+ *                       grid-wide barriers between the steps; needs floating-
+ *                       point accumulation. A barrier that waits longer than
+ *                       about 2 s ends the decode with MBP_ETIMEOUT;
+ *  MBP_SCHED_AUTO       (default) STREAMING, which measures faster on GB300
+ *                       for the benchmark workload.
+ */
+enum { MBP_SCHED_AUTO = 0, MBP_SCHED_STREAMING = 1, MBP_SCHED_RESIDENT = 2 };
 
 /* One binary m x n matrix in compressed sparse rows, host memory, 0-based. */
 typedef struct {
@@ -96,7 +113,7 @@ typedef struct {
                              each frame ran (float for F32, double for F64); NULL to skip */
   uint8_t* synd_ok;       /* optional device [F][u]: 1 where H_l x_hat = z^l for the output bits */
   int32_t accumulate;     /* MBP_ACC_AUTO (default), MBP_ACC_FLOAT or MBP_ACC_FIXED */
-  int32_t reserved;
+  int32_t schedule;       /* MBP_SCHED_AUTO (default), MBP_SCHED_STREAMING or MBP_SCHED_RESIDENT */
 } mbp_opts;
 
 /* Fill *opts with the defaults above (F32, early exit, l_max 20, no workspace). */
@@ -239,7 +256,8 @@ enum {
   MBP_KERNEL_RETIRE = 3,    /* retire finished frames */
   MBP_KERNEL_SETUP = 4,     /* channel LLRs, syndrome bits and tile state into the workspace */
   MBP_KERNEL_OUTPUT = 5,    /* output bits and soft values */
-  MBP_KERNEL_FAMILIES = 6
+  MBP_KERNEL_PERSISTENT = 6,/* the resident schedule's single kernel (all steps of every iteration) */
+  MBP_KERNEL_FAMILIES = 7
 };
 int mbp_profile_enable(int on);
 int mbp_profile_get(int family, int64_t* launches, double* milliseconds);

@@ -24,6 +24,7 @@ from ._build import LIB, build, up_to_date
 
 __all__ = [
     "build", "library_path", "MBPError", "Codes", "MSG_F32", "MSG_F64", "ACC_AUTO", "ACC_FLOAT", "ACC_FIXED",
+    "SCHED_AUTO", "SCHED_STREAMING", "SCHED_RESIDENT",
     "mbp_create_codes", "mbp_destroy_codes", "mbp_syndrome", "mbp_bsc_llr", "mbp_decode_workspace_size",
     "mbp_decode_batch", "mbp_decode_bsc", "mbp_decode_bsc_host", "mbp_export_c2v", "mbp_version",
     "split_syndromes", "join_syndromes", "mbp_profile_enable", "mbp_profile_get", "KERNEL_FAMILIES",
@@ -31,6 +32,7 @@ __all__ = [
 
 MSG_F32, MSG_F64 = 0, 1
 ACC_AUTO, ACC_FLOAT, ACC_FIXED = 0, 1, 2
+SCHED_AUTO, SCHED_STREAMING, SCHED_RESIDENT = 0, 1, 2
 _STATUS = {0: "MBP_OK", 1: "MBP_EINVAL", 2: "MBP_ENOMEM", 3: "MBP_ECUDA", 4: "MBP_ETIMEOUT", 5: "MBP_EUNSUPPORTED"}
 
 
@@ -49,7 +51,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("msg_dtype", ctypes.c_int32), ("early_exit", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("host_io", ctypes.c_int32), ("l_max", ctypes.c_double), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("soft_out", ctypes.c_void_p), ("synd_ok", ctypes.c_void_p),
-                ("accumulate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("accumulate", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -215,11 +217,12 @@ def mbp_bsc_llr(y_bits: torch.Tensor, qber: torch.Tensor, n: int, dtype=torch.fl
 
 
 def _opts(msg_dtype, l_max, early_exit, validate, host_io, workspace=None, soft=None, synd=None,
-          accumulate=ACC_AUTO) -> _Opts:
+          accumulate=ACC_AUTO, schedule=SCHED_AUTO) -> _Opts:
     o = _Opts()
     _load().mbp_default_opts(ctypes.byref(o))
     o.msg_dtype = msg_dtype
     o.accumulate = int(accumulate)
+    o.schedule = int(schedule)
     o.l_max = float(l_max)
     o.early_exit = int(bool(early_exit))
     o.validate = int(bool(validate))
@@ -247,7 +250,7 @@ def _workspace(codes, F, msg_dtype, host_io, workspace, device):
 
 
 def _decode(entry, codes, F, inputs, z_bits, max_iter, msg_dtype, l_max, early_exit, validate, want_soft,
-            want_synd, workspace, device, stream, accumulate=ACC_AUTO):
+            want_synd, workspace, device, stream, accumulate=ACC_AUTO, schedule=SCHED_AUTO):
     workspace = _workspace(codes, F, msg_dtype, False, workspace, device)
     fdt = torch.float64 if msg_dtype == MSG_F64 else torch.float32
     xh = torch.empty((F, _words(codes.n)), dtype=torch.int32, device=device)
@@ -255,7 +258,7 @@ def _decode(entry, codes, F, inputs, z_bits, max_iter, msg_dtype, l_max, early_e
     ok = torch.empty(F, dtype=torch.uint8, device=device)
     soft = torch.empty((F, codes.n), dtype=fdt, device=device) if want_soft else None
     synd = torch.empty((F, codes.u), dtype=torch.uint8, device=device) if want_synd else None
-    o = _opts(msg_dtype, l_max, early_exit, validate, False, workspace, soft, synd, accumulate)
+    o = _opts(msg_dtype, l_max, early_exit, validate, False, workspace, soft, synd, accumulate, schedule)
     z = z_bits.contiguous()
     _check(entry(codes.handle, F, *[_ptr(t) for t in inputs], _ptr(z), int(max_iter), ctypes.byref(o),
                  _ptr(xh), _ptr(it), _ptr(ok), _stream_ptr(stream)))
@@ -270,31 +273,31 @@ def _decode(entry, codes, F, inputs, z_bits, max_iter, msg_dtype, l_max, early_e
 def mbp_decode_batch(codes: Codes, llr: torch.Tensor, z_bits: torch.Tensor, max_iter: int, *, l_max: float = 20.0,
                      early_exit: bool = True, validate: bool = False, want_soft: bool = False,
                      want_synd: bool = False, workspace: torch.Tensor | None = None, stream=None,
-                     accumulate: int = ACC_AUTO) -> dict:
+                     accumulate: int = ACC_AUTO, schedule: int = SCHED_AUTO) -> dict:
     """Decode F frames from channel LLRs (float32 -> FP32 messages, float64 -> FP64 messages)."""
     x = llr.contiguous()
     msg = MSG_F64 if x.dtype == torch.float64 else MSG_F32
     if x.dtype not in (torch.float32, torch.float64):
         raise TypeError("llr must be float32 or float64")
     return _decode(_load().mbp_decode_batch, codes, x.shape[0], [x], z_bits, max_iter, msg, l_max, early_exit,
-                   validate, want_soft, want_synd, workspace, x.device, stream, accumulate)
+                   validate, want_soft, want_synd, workspace, x.device, stream, accumulate, schedule)
 
 
 def mbp_decode_bsc(codes: Codes, y_bits: torch.Tensor, qber: torch.Tensor, z_bits: torch.Tensor, max_iter: int, *,
                    msg_dtype: int = MSG_F32, l_max: float = 20.0, early_exit: bool = True, want_soft: bool = False,
                    want_synd: bool = False, workspace: torch.Tensor | None = None, stream=None,
-                   accumulate: int = ACC_AUTO) -> dict:
+                   accumulate: int = ACC_AUTO, schedule: int = SCHED_AUTO) -> dict:
     """Decode F BSC frames from Bob's bits and per-frame QBER (eq. 5 formed on the device)."""
     y = y_bits.contiguous()
     q = qber.to(torch.float64).contiguous()
     return _decode(_load().mbp_decode_bsc, codes, y.shape[0], [y, q], z_bits, max_iter, msg_dtype, l_max,
-                   early_exit, False, want_soft, want_synd, workspace, y.device, stream, accumulate)
+                   early_exit, False, want_soft, want_synd, workspace, y.device, stream, accumulate, schedule)
 
 
 def mbp_decode_bsc_host(codes: Codes, y_bits: np.ndarray, qber: np.ndarray, z_bits: np.ndarray, max_iter: int, *,
                         msg_dtype: int = MSG_F32, l_max: float = 20.0, early_exit: bool = True,
                         workspace: torch.Tensor | None = None, out: dict | None = None, stream=None,
-                        device=None, accumulate: int = ACC_AUTO) -> dict:
+                        device=None, accumulate: int = ACC_AUTO, schedule: int = SCHED_AUTO) -> dict:
     """Host-memory variant: inputs and outputs are numpy arrays (or pinned CPU tensors)."""
     y = y_bits if isinstance(y_bits, torch.Tensor) else np.ascontiguousarray(y_bits, dtype=np.uint32)
     q = qber if isinstance(qber, torch.Tensor) else np.ascontiguousarray(qber, dtype=np.float64)
@@ -307,7 +310,7 @@ def mbp_decode_bsc_host(codes: Codes, y_bits: np.ndarray, qber: np.ndarray, z_bi
     if out is None:
         out = dict(x_hat_bits=np.zeros((F, _words(codes.n)), np.uint32), iters=np.zeros(F, np.int32),
                    success=np.zeros(F, np.uint8))
-    o = _opts(msg_dtype, l_max, early_exit, False, True, workspace, accumulate=accumulate)
+    o = _opts(msg_dtype, l_max, early_exit, False, True, workspace, accumulate=accumulate, schedule=schedule)
     _check(_load().mbp_decode_bsc_host(codes.handle, F, _ptr(y), _ptr(q), _ptr(z), int(max_iter), ctypes.byref(o),
                                        _ptr(out["x_hat_bits"]), _ptr(out["iters"]), _ptr(out["success"]),
                                        _stream_ptr(stream)))
@@ -325,7 +328,7 @@ def mbp_export_c2v(codes: Codes, F: int, workspace: torch.Tensor, frame: int, ms
     return out
 
 
-KERNEL_FAMILIES = ("check", "variable", "syndrome", "retire", "setup", "output")
+KERNEL_FAMILIES = ("check", "variable", "syndrome", "retire", "setup", "output", "persistent")
 
 
 def mbp_profile_enable(on: bool = True):

@@ -135,6 +135,8 @@ int validate_opts(const mbp_opts* o) {
   REQUIRE(std::isfinite(o->l_max) && o->l_max > 0, "l_max must be finite and > 0");
   REQUIRE(o->accumulate == MBP_ACC_AUTO || o->accumulate == MBP_ACC_FLOAT || o->accumulate == MBP_ACC_FIXED,
           "unknown accumulate mode %d", o->accumulate);
+  REQUIRE(o->schedule == MBP_SCHED_AUTO || o->schedule == MBP_SCHED_STREAMING || o->schedule == MBP_SCHED_RESIDENT,
+          "unknown schedule %d", o->schedule);
   return MBP_OK;
 }
 
@@ -237,22 +239,41 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   int32_t max_deg = 0;
   for (int64_t r = 0; r < m_tot; ++r) max_deg = std::max(max_deg, row_deg[r]);
   d.max_row_deg = max_deg;
+  // Slices are built over the stacked rows ordered by degree (ties keep the stacked
+  // order), so the 4 rows of a slice nearly always share one degree and need no
+  // padding. The order is internal: syndrome bits are looked up through
+  // perm_mat / perm_local, and C2V exports go through edge_slot.
+  std::vector<int32_t> order(m_tot);
+  for (int64_t p = 0; p < m_tot; ++p) order[p] = static_cast<int32_t>(p);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return row_deg[a] < row_deg[b]; });
+  std::vector<uint8_t> perm_mat(std::max<int64_t>(m_tot, 1));
+  std::vector<int32_t> perm_local(std::max<int64_t>(m_tot, 1));
+  for (int64_t p = 0; p < m_tot; ++p) {
+    const int32_t r = order[p];
+    perm_mat[p] = row_mat[r];
+    perm_local[p] = r - d.row_first[row_mat[r]];
+  }
   std::vector<int32_t> slice_base(n_slices + 1);
+  std::vector<uint8_t> slice_full(std::max<int32_t>(n_slices, 1));
   slice_base[0] = 0;
   for (int32_t s = 0; s < n_slices; ++s) {
-    int32_t dm = 0;
+    int32_t dm = 0, dmin = INT32_MAX;
     for (int q = 0; q < kSliceRows; ++q) {
-      int64_t r = int64_t(s) * kSliceRows + q;
-      if (r < m_tot) dm = std::max(dm, row_deg[r]);
+      int64_t p = int64_t(s) * kSliceRows + q;
+      const int32_t dq = p < m_tot ? row_deg[order[p]] : -1;
+      dm = std::max(dm, dq);
+      dmin = std::min(dmin, dq);
     }
+    slice_full[s] = uint8_t(dmin == dm);  // every row present and of the slice's degree
     int64_t next = int64_t(slice_base[s]) + int64_t(dm) * kSliceRows;
     REQUIRE(next <= INT32_MAX / 2, "code too large");
     slice_base[s + 1] = static_cast<int32_t>(next);
   }
   d.s_tot = slice_base[n_slices];
   std::vector<int32_t> slot_col(std::max<int64_t>(d.s_tot, 1), -1), edge_slot(std::max<int64_t>(e_tot, 1));
-  for (int64_t r = 0; r < m_tot; ++r) {
-    int32_t s = static_cast<int32_t>(r / kSliceRows), q = static_cast<int32_t>(r % kSliceRows);
+  for (int64_t p = 0; p < m_tot; ++p) {
+    const int32_t r = order[p];
+    int32_t s = static_cast<int32_t>(p / kSliceRows), q = static_cast<int32_t>(p % kSliceRows);
     for (int32_t k = 0; k < row_deg[r]; ++k) {
       int32_t slot = slice_base[s] + k * kSliceRows + q;
       slot_col[slot] = col_idx[row_ptr[r] + k];
@@ -279,7 +300,8 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
       {slice_base.data(), slice_base.size() * 4, 0}, {slot_col.data(), slot_col.size() * 4, 0},
       {col_ptr.data(), col_ptr.size() * 4, 0},       {col_slot.data(), col_slot.size() * 4, 0},
       {row_ptr.data(), row_ptr.size() * 4, 0},       {col_idx.data(), col_idx.size() * 4, 0},
-      {edge_slot.data(), edge_slot.size() * 4, 0},   {row_mat.data(), row_mat.size(), 0}};
+      {edge_slot.data(), edge_slot.size() * 4, 0},   {perm_mat.data(), perm_mat.size(), 0},
+      {perm_local.data(), perm_local.size() * 4, 0}, {slice_full.data(), slice_full.size(), 0}};
   size_t total = 0;
   for (auto& p : parts) {
     p.off = total;
@@ -313,6 +335,8 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   d.col_idx = reinterpret_cast<const int32_t*>(base + parts[5].off);
   d.edge_slot = reinterpret_cast<const int32_t*>(base + parts[6].off);
   d.row_mat = reinterpret_cast<const uint8_t*>(base + parts[7].off);
+  d.row_local = reinterpret_cast<const int32_t*>(base + parts[8].off);
+  d.slice_full = reinterpret_cast<const uint8_t*>(base + parts[9].off);
   h->d = d;
   *out = h;
   return MBP_OK;
@@ -401,6 +425,7 @@ static int decode_common(const mbp_codes* codes, int F, const void* llr, const u
   a.max_iter = max_iter;
   a.early_exit = opts->early_exit;
   a.accumulate = opts->accumulate;
+  a.schedule = opts->schedule;
   a.validate = opts->validate;
   a.l_max = opts->l_max;
   a.x_hat_bits = x_hat_bits;
@@ -458,6 +483,7 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   a.max_iter = max_iter;
   a.early_exit = opts->early_exit;
   a.accumulate = opts->accumulate;
+  a.schedule = opts->schedule;
   a.validate = opts->validate;
   a.l_max = opts->l_max;
   a.x_hat_bits = st.io_xhat;
@@ -511,6 +537,7 @@ int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits,
   a.max_iter = max_iter;
   a.early_exit = opts->early_exit;
   a.accumulate = opts->accumulate;
+  a.schedule = opts->schedule;
   a.validate = 0;
   a.l_max = opts->l_max;
   a.x_hat_bits = x_hat_bits;

@@ -2,11 +2,13 @@
 //
 // Device layout of the stacked code [H_1; ...; H_u] (Section 2: u matrices of
 // size m_l x n sharing the n variable nodes):
-//   * stacked row r = row_first[l] + j is row j of H_l;
-//   * rows are grouped in slices of kSliceRows consecutive rows; a slice whose
-//     longest row has d edges owns kSliceRows * d edge "slots", slot
-//     slice_base[s] + k * kSliceRows + q holding edge k of row kSliceRows*s + q
-//     (slot_col = -1 where that row is shorter: padding);
+//   * stacked row r = row_first[l] + j is row j of H_l (the CSR arrays);
+//   * for the decoder the rows are put in degree order (position p) and grouped
+//     in slices of kSliceRows positions; a slice whose longest row has d edges
+//     owns kSliceRows * d edge "slots", slot slice_base[s] + k * kSliceRows + q
+//     holding edge k of the row at position kSliceRows*s + q (slot_col = -1
+//     where that row is shorter: padding); row_mat/row_local name the matrix and
+//     row of each position;
 //   * every per-edge message array is indexed [tile][slot][lane]: kLanes frames
 //     ("lanes") are interleaved so that one edge of kLanes frames is one
 //     contiguous 32-byte (FP32) or 64-byte (FP64) vector;
@@ -46,7 +48,9 @@ struct DevCode {
   const int32_t* row_ptr;     // [m_tot + 1] stacked CSR
   const int32_t* col_idx;     // [e_tot]
   const int32_t* edge_slot;   // [e_tot] stacked CSR edge -> slot
-  const uint8_t* row_mat;     // [m_tot] matrix index of each stacked row
+  const uint8_t* row_mat;     // [m_tot] matrix l of the row in slice position p
+  const int32_t* row_local;   // [m_tot] row index j inside H_l of the row in slice position p
+  const uint8_t* slice_full;  // [n_slices] 1 if every row of the slice has the slice's degree
 };
 
 // Per-call decoder state carved out of the caller's workspace.
@@ -62,6 +66,7 @@ struct DevState {
   uint32_t* fail;     // [n_tiles][u] lanes whose hard decision violates some check of H_l
   double* llr_mag;    // [F] ln((1 - e)/e) for the BSC entry points
   int32_t* counters;  // [4]: unfinished tiles, non-finite flag
+  void* ctl;          // control block of the resident schedule (barrier, retirement)
   // staging for mbp_decode_bsc_host
   uint32_t* io_y;
   double* io_qber;
@@ -101,6 +106,7 @@ struct DecodeArgs {
   int max_iter;
   int early_exit;
   int accumulate;
+  int schedule;
   int validate;
   double l_max;
   uint32_t* x_hat_bits;

@@ -100,15 +100,19 @@ def test_bsc_llr_matches_oracle(mbp):
 
 # ------------------------------------------------------- whole decoder
 
-MODES = ["f64", "f32-float", "f32-fixed"]
+MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident"]
 
 
 def mode_args(mbp, mode):
     if mode == "f64":
-        return dict(msg_dtype=mbp.MSG_F64, accumulate=mbp.ACC_FLOAT)
+        return dict(msg_dtype=mbp.MSG_F64, accumulate=mbp.ACC_FLOAT, schedule=mbp.SCHED_STREAMING)
     if mode == "f32-float":
-        return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FLOAT)
-    return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FIXED)
+        return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FLOAT, schedule=mbp.SCHED_STREAMING)
+    if mode == "f32-fixed":
+        return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FIXED, schedule=mbp.SCHED_STREAMING)
+    if mode == "f64-resident":
+        return dict(msg_dtype=mbp.MSG_F64, schedule=mbp.SCHED_RESIDENT)
+    return dict(msg_dtype=mbp.MSG_F32, schedule=mbp.SCHED_RESIDENT)
 
 
 def _decode_both(mbp, w, max_iter, msg64, early_exit=True, want_lv=False, threads=8, mode=None):
@@ -128,7 +132,7 @@ def _decode_both(mbp, w, max_iter, msg64, early_exit=True, want_lv=False, thread
 @pytest.mark.parametrize("mode", MODES)
 def test_rate05_n1024_u2_qber3(mbp, mode):
     """n=1024, m=512 per matrix, d_v=3, u=2, QBER 3%, 64 frames, max 50 iterations, seed 0."""
-    msg64 = mode == "f64"
+    msg64 = mode.startswith("f64")
     w = Workload(1024, 512, {3: 1.0}, 2, 0, 64, 0.03)
     _, out, ref = _decode_both(mbp, w, 50, msg64, want_lv=True, mode=mode)
     check_outputs_bit_exact(out, ref, w.n, fp64=msg64)
@@ -141,7 +145,7 @@ def test_rate05_n1024_u2_qber3(mbp, mode):
 @pytest.mark.parametrize("t", [1, 2, 3, 4, 5])
 def test_messages_within_tolerance_first_iterations(mbp, mode, t):
     """C2V and L_V after t flooding iterations (no early exit), 13 frames = 2 tiles with a ragged tail."""
-    msg64 = mode == "f64"
+    msg64 = mode.startswith("f64")
     w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 13, 0.05)
     codes, out, ref = _decode_both(mbp, w, t, msg64, early_exit=False, want_lv=True, mode=mode)
     tol = TOL_F64 if msg64 else TOL_F32
@@ -153,7 +157,7 @@ def test_messages_within_tolerance_first_iterations(mbp, mode, t):
     assert np.array_equal(out["iters"].cpu().numpy(), np.full(w.F, t))
 
 
-@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed"])
+@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed", "f32-resident"])
 def test_rate07_n65536_first_iterations_fp32(mbp, mode):
     """The n=65536 rate-0.7 code: FP32 C2V/L_V within 1e-3 of the oracle over iterations 1..5."""
     w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 3, 0.02)
@@ -170,7 +174,7 @@ def test_rate07_n65536_first_iterations_fp32(mbp, mode):
             assert np.max(np.abs(c - ref["c2v"][f])) <= TOL_F32
 
 
-@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed"])
+@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed", "f32-resident"])
 def test_rate07_n65536_subset_bit_exact(mbp, mode):
     """n=65536, R=0.7, d_v {2,3,8}, u=2, QBER 2%: 64 frames, max 60 iterations."""
     w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 64, 0.02)
@@ -220,11 +224,12 @@ def test_edge_cases(mbp):
     codes = mbp.mbp_create_codes(H)
     zg = gpu_syndrome(mbp, codes, x)
     assert np.array_equal(host_u32(zg), np.concatenate([a.reshape(-1) for a in z]))
+    ref = orc.decode(H, orc.bsc_llr(y, n, e), z, 20, want_synd=True, want_lv=True)
     for msg64 in (True, False):
-        out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(y)), dev(e), zg, 20, want_synd=True, want_soft=True,
-                                 msg_dtype=mbp.MSG_F64 if msg64 else mbp.MSG_F32)
-        ref = orc.decode(H, orc.bsc_llr(y, n, e), z, 20, want_synd=True, want_lv=True)
-        check_outputs_bit_exact(out, ref, n, fp64=msg64)
+        for sched in (mbp.SCHED_STREAMING, mbp.SCHED_RESIDENT):
+            out = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(y)), dev(e), zg, 20, want_synd=True, want_soft=True,
+                                     msg_dtype=mbp.MSG_F64 if msg64 else mbp.MSG_F32, schedule=sched)
+            check_outputs_bit_exact(out, ref, n, fp64=msg64)
 
 
 def test_empty_batch_and_zero_iterations(mbp):
@@ -250,10 +255,11 @@ def test_noise_free_frames_stop_at_iteration_zero(mbp):
     assert np.array_equal(host_u32(out["x_hat_bits"]), w.x)
 
 
-def test_failing_frames_fp64_match_oracle(mbp):
+@pytest.mark.parametrize("mode", ["f64", "f64-resident"])
+def test_failing_frames_fp64_match_oracle(mbp, mode):
     """Above the decoding threshold: failures report success=0, iters=max_iter, last hard decision."""
     w = Workload(1024, 512, {3: 1.0}, 2, 0, 16, 0.2)
-    _, out, ref = _decode_both(mbp, w, 15, True)
+    _, out, ref = _decode_both(mbp, w, 15, True, mode=mode)
     check_outputs_bit_exact(out, ref, w.n, fp64=True)
     assert (ref["success"] == 0).any()
 
@@ -359,3 +365,37 @@ def test_accumulation_modes_agree(mbp):
     ok = (a["success"] == 1) & (b["success"] == 1)
     assert torch.equal(a["x_hat_bits"][ok], b["x_hat_bits"][ok])
     assert int(ok.sum()) >= 35
+
+
+@pytest.mark.parametrize("early_exit", [True, False])
+def test_schedules_agree_bit_for_bit(mbp, early_exit):
+    """The streaming and resident schedules run the same arithmetic in the same order."""
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 3, 7, 45, 0.06)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y, e = dev(u32_to_i32(w.y)), dev(w.e)
+    a = mbp.mbp_decode_bsc(codes, y, e, z, 25, early_exit=early_exit, want_soft=True, want_synd=True,
+                           schedule=mbp.SCHED_STREAMING)
+    b = mbp.mbp_decode_bsc(codes, y, e, z, 25, early_exit=early_exit, want_soft=True, want_synd=True,
+                           schedule=mbp.SCHED_RESIDENT)
+    for k in ("x_hat_bits", "iters", "success", "synd_ok", "soft"):
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_resident_barrier_timeout_reports_etimeout(mbp, monkeypatch):
+    """A barrier that waits for an arrival that never comes gives up, and the host gets MBP_ETIMEOUT;
+    the context stays usable for the next decode."""
+    w = Workload(512, 200, {3: 1.0}, 2, 3, 16, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    y, e = dev(u32_to_i32(w.y)), dev(w.e)
+    monkeypatch.setenv("MBP_TEST_BARRIER_EXTRA_ARRIVALS", "1")
+    monkeypatch.setenv("MBP_TEST_BARRIER_TIMEOUT_US", "50000")
+    with pytest.raises(mbp.MBPError) as ei:
+        mbp.mbp_decode_bsc(codes, y, e, z, 10, schedule=mbp.SCHED_RESIDENT)
+    assert ei.value.status == 4
+    monkeypatch.delenv("MBP_TEST_BARRIER_EXTRA_ARRIVALS")
+    monkeypatch.delenv("MBP_TEST_BARRIER_TIMEOUT_US")
+    out = mbp.mbp_decode_bsc(codes, y, e, z, 10, schedule=mbp.SCHED_RESIDENT)
+    ref = mbp.mbp_decode_bsc(codes, y, e, z, 10, schedule=mbp.SCHED_STREAMING)
+    assert torch.equal(out["x_hat_bits"], ref["x_hat_bits"]) and torch.equal(out["iters"], ref["iters"])
