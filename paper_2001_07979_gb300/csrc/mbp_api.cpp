@@ -221,8 +221,6 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
     d.m[l] = H[l].m;
     d.row_first[l + 1] = d.row_first[l] + H[l].m;
   }
-  const int32_t n_slices = static_cast<int32_t>((m_tot + kSliceRows - 1) / kSliceRows);
-  d.n_slices = n_slices;
   std::vector<int32_t> row_ptr(m_tot + 1), col_idx(std::max<int64_t>(e_tot, 1)), row_deg(m_tot);
   std::vector<uint8_t> row_mat(std::max<int64_t>(m_tot, 1));
   {
@@ -239,43 +237,29 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   int32_t max_deg = 0;
   for (int64_t r = 0; r < m_tot; ++r) max_deg = std::max(max_deg, row_deg[r]);
   d.max_row_deg = max_deg;
-  // Slices are built over the stacked rows ordered by degree (ties keep the stacked
-  // order), so the 4 rows of a slice nearly always share one degree and need no
-  // padding. The order is internal: syndrome bits are looked up through
-  // perm_mat / perm_local, and C2V exports go through edge_slot.
+  // The decoder visits the stacked rows in degree order (ties keep the stacked
+  // order): row position p owns the slots slice_base[p] .. slice_base[p+1] - 1.
+  // The order is internal: syndrome bits are looked up through perm_mat /
+  // perm_local, and C2V exports go through edge_slot.
   std::vector<int32_t> order(m_tot);
   for (int64_t p = 0; p < m_tot; ++p) order[p] = static_cast<int32_t>(p);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return row_deg[a] < row_deg[b]; });
   std::vector<uint8_t> perm_mat(std::max<int64_t>(m_tot, 1));
   std::vector<int32_t> perm_local(std::max<int64_t>(m_tot, 1));
+  std::vector<int32_t> slice_base(m_tot + 1);
+  slice_base[0] = 0;
   for (int64_t p = 0; p < m_tot; ++p) {
     const int32_t r = order[p];
     perm_mat[p] = row_mat[r];
     perm_local[p] = r - d.row_first[row_mat[r]];
+    slice_base[p + 1] = slice_base[p] + row_deg[r];
   }
-  std::vector<int32_t> slice_base(n_slices + 1);
-  std::vector<uint8_t> slice_full(std::max<int32_t>(n_slices, 1));
-  slice_base[0] = 0;
-  for (int32_t s = 0; s < n_slices; ++s) {
-    int32_t dm = 0, dmin = INT32_MAX;
-    for (int q = 0; q < kSliceRows; ++q) {
-      int64_t p = int64_t(s) * kSliceRows + q;
-      const int32_t dq = p < m_tot ? row_deg[order[p]] : -1;
-      dm = std::max(dm, dq);
-      dmin = std::min(dmin, dq);
-    }
-    slice_full[s] = uint8_t(dmin == dm);  // every row present and of the slice's degree
-    int64_t next = int64_t(slice_base[s]) + int64_t(dm) * kSliceRows;
-    REQUIRE(next <= INT32_MAX / 2, "code too large");
-    slice_base[s + 1] = static_cast<int32_t>(next);
-  }
-  d.s_tot = slice_base[n_slices];
+  d.s_tot = slice_base[m_tot];
   std::vector<int32_t> slot_col(std::max<int64_t>(d.s_tot, 1), -1), edge_slot(std::max<int64_t>(e_tot, 1));
   for (int64_t p = 0; p < m_tot; ++p) {
     const int32_t r = order[p];
-    int32_t s = static_cast<int32_t>(p / kSliceRows), q = static_cast<int32_t>(p % kSliceRows);
     for (int32_t k = 0; k < row_deg[r]; ++k) {
-      int32_t slot = slice_base[s] + k * kSliceRows + q;
+      const int32_t slot = slice_base[p] + k;
       slot_col[slot] = col_idx[row_ptr[r] + k];
       edge_slot[row_ptr[r] + k] = slot;
     }
@@ -301,7 +285,7 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
       {col_ptr.data(), col_ptr.size() * 4, 0},       {col_slot.data(), col_slot.size() * 4, 0},
       {row_ptr.data(), row_ptr.size() * 4, 0},       {col_idx.data(), col_idx.size() * 4, 0},
       {edge_slot.data(), edge_slot.size() * 4, 0},   {perm_mat.data(), perm_mat.size(), 0},
-      {perm_local.data(), perm_local.size() * 4, 0}, {slice_full.data(), slice_full.size(), 0}};
+      {perm_local.data(), perm_local.size() * 4, 0}};
   size_t total = 0;
   for (auto& p : parts) {
     p.off = total;
@@ -336,7 +320,6 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   d.edge_slot = reinterpret_cast<const int32_t*>(base + parts[6].off);
   d.row_mat = reinterpret_cast<const uint8_t*>(base + parts[7].off);
   d.row_local = reinterpret_cast<const int32_t*>(base + parts[8].off);
-  d.slice_full = reinterpret_cast<const uint8_t*>(base + parts[9].off);
   h->d = d;
   *out = h;
   return MBP_OK;

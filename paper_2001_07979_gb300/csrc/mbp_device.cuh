@@ -1,0 +1,352 @@
+// Device building blocks of libmbp (sm_103a), shared by the streaming and the
+// resident schedules.
+//
+// Data layout (per decode, inside the caller's workspace): kLanes = 32 frames
+// form a tile; every per-edge or per-node array stores the tile's 32 frames of
+// one edge or node contiguously, so each random access moves one 128-byte line
+// (FP32) and one warp (lane = frame) handles one check row or one variable
+// node of one tile.
+//
+// Check-node arithmetic. For a check with incoming V2C values v_k, eq. (6) gives
+//   |C2V_k| = 2 atanh( prod_{r != k} tanh(|v_r| / 2) ),
+//   sign(C2V_k) = (-1)^{z_j} prod_{r != k} sign(v_r).
+// With delta_r = (1 - tanh(|v_r| / 2)) / 2 = 1 / (1 + e^{|v_r|}) the product
+// becomes 1 - 2 D_k with D_k = (+)_{r != k} delta_r under x (+) y = x + y - 2 x y
+// (the complement of a product, halved), and 2 atanh(1 - 2 D) = ln((1 - D) / D).
+// Working with delta keeps full relative precision for reliable messages
+// (delta ~ e^{-|v|}) where tanh rounds to 1 in FP32. The exclusion r != k uses
+// prefix and suffix (+)-combinations, never a division. Per edge this is two
+// MUFU operations in, two out (exp + reciprocal, reciprocal + log).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mbp_internal.h"
+
+namespace mbp {
+namespace dev {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kSign = 0x80000000u;
+
+// Approximate MUFU forms with denormals flushed (the decoder's values stay normal
+// or are meant to vanish), straight from the PTX ISA.
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Check-node arithmetic in the halved complement form (see the file header).
+// FP32 messages are kept in log2 units inside the decoder (LLR * log2 e), so
+// e^{|v|} is one ex2 and the natural log is one lg2: delta = rcp(1 + ex2(a)),
+// magnitude = lg2((1 - D) * rcp(D)). FP64 keeps natural units and the libm
+// exp/log. kToInternal / kToLLR convert at the boundary (set-up and outputs).
+template <typename M>
+struct Arith;
+
+template <>
+struct Arith<float> {
+  static constexpr double kToInternal = 1.4426950408889634074;  // log2(e)
+  static constexpr float kToLLR = 0.69314718055994530942f;      // ln(2)
+  static __device__ __forceinline__ float delta(float a) { return rcp_ftz(1.0f + ex2_ftz(a)); }
+  static __device__ __forceinline__ float oplus(float p, float d) { return fmaf(d, fmaf(-2.0f, p, 1.0f), p); }
+  static __device__ __forceinline__ float mag(float D) { return lg2_ftz((1.0f - D) * rcp_ftz(D)); }
+  // min(|v|, L) = L * sat(|v| / L) on the FMA pipe (.sat clamps to [0, 1])
+  static __device__ __forceinline__ float clip_abs(float v, float L, float invL) {
+    return __saturatef(fabsf(v) * invL) * L;
+  }
+  // min(mag(D), L); .sat also maps a rounding-level negative magnitude to +0
+  static __device__ __forceinline__ float clipped_mag(float D, float L, float invL) {
+    return __saturatef(mag(D) * invL) * L;
+  }
+};
+
+template <>
+struct Arith<double> {
+  static constexpr double kToInternal = 1.0;
+  static constexpr double kToLLR = 1.0;
+  static __device__ __forceinline__ double delta(double a) { return 1.0 / (1.0 + exp(a)); }
+  static __device__ __forceinline__ double oplus(double p, double d) { return fma(d, fma(-2.0, p, 1.0), p); }
+  static __device__ __forceinline__ double mag(double D) { return log((1.0 - D) / D); }
+  static __device__ __forceinline__ double clip_abs(double v, double L, double) { return fmin(fabs(v), L); }
+  static __device__ __forceinline__ double clipped_mag(double D, double L, double) {
+    return fmax(fmin(mag(D), L), 0.0);
+  }
+};
+
+// Sign-bit access: sign_word returns a 32-bit word whose top bit is the sign.
+template <typename M>
+struct Bits;
+
+template <>
+struct Bits<float> {
+  static __device__ __forceinline__ uint32_t sign_word(float x) { return __float_as_uint(x); }
+  static __device__ __forceinline__ float with_sign(float m, uint32_t sign) {
+    return __uint_as_float(__float_as_uint(m) | sign);
+  }
+  // |m| with the top bit of `word` as sign
+  static __device__ __forceinline__ float copy_sign(float m, uint32_t word) {
+    return __uint_as_float((__float_as_uint(m) & ~kSign) | (word & kSign));
+  }
+};
+
+template <>
+struct Bits<double> {
+  static __device__ __forceinline__ uint32_t sign_word(double x) { return uint32_t(__double2hiint(x)); }
+  static __device__ __forceinline__ double with_sign(double m, uint32_t sign) {
+    return __hiloint2double(int(uint32_t(__double2hiint(m)) | sign), __double2loint(m));
+  }
+  static __device__ __forceinline__ double copy_sign(double m, uint32_t word) {
+    const uint32_t hi = (uint32_t(__double2hiint(m)) & ~kSign) | (word & kSign);
+    return __hiloint2double(int(hi), __double2loint(m));
+  }
+};
+
+// Memory policies.
+//  kPolStream:   streaming kernels, which only read data written by earlier
+//                launches: posterior through the read-only path, messages
+//                loaded and stored evict-first (touched once per iteration).
+//  kPolCoherent: the persistent resident schedule, whose phases read data
+//                written by other blocks of the same launch: every such load
+//                goes to L2 (.cg, no stale L1 line) and messages stay in L2.
+constexpr int kPolStream = 0, kPolCoherent = 1;
+template <int POL, typename T>
+__device__ __forceinline__ T ld_state(const T* p) {
+  if constexpr (POL == kPolCoherent) return __ldcg(p);
+  else return __ldg(p);
+}
+template <int POL, typename T>
+__device__ __forceinline__ T ld_msg(const T* p) {
+  if constexpr (POL == kPolCoherent) return __ldcg(p);
+  else return __ldcs(p);
+}
+template <int POL, typename T>
+__device__ __forceinline__ void st_msg(T* p, T v) {
+  if constexpr (POL == kPolCoherent) __stcg(p, v);
+  else __stcs(p, v);
+}
+
+// ------------------------------------------------------------- eq. (6)
+
+// The check-node update of eq. (6) for one row and one lane (frame).
+// Every load of the row is issued before the first use: the row's columns, then
+// the posterior gathers and the old messages, so a warp waits for two memory
+// round trips per row rather than two per edge. CHECKED = false is the body for
+// rows of exactly D edges (no per-edge tests).
+//
+// Signs travel in IEEE sign bits: the row's sign parity (with z_j) is the XOR
+// of the V2C words' top bits, and each edge's own sign is kept in the sign bit
+// of its delta, whose magnitude the (+) operations read through |.|.
+//
+// FIXED: also add each edge's change of message, q(C2V_new) - q(C2V_old) with
+// q(x) = round(x * qscale), to the posterior accumulator lacc of its variable
+// node (a 32-bit red.global.add in L2). Integer addition is associative, so
+// the accumulated sum sum_e q(C2V_e) is exact and independent of the order of
+// the atomics; finalize_kernel turns it into L_V.
+template <typename M, int D, bool FIXED, bool CHECKED, int POL>
+__device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, const M* __restrict__ gsrc,
+                                       M* __restrict__ msg, int first_iter, uint32_t par, bool store, M l_max,
+                                       M inv_l_max, int32_t* __restrict__ lacc, float qscale) {
+  int col[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : -1;
+  M v[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : M(0);
+  [[maybe_unused]] M old[FIXED ? D : 1];
+  if (!first_iter) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const M o = (!CHECKED || col[k] >= 0) ? ld_msg<POL>(msg + k * kLanes) : M(0);
+      if constexpr (FIXED) old[k] = o;
+      v[k] -= o;
+    }
+  } else if constexpr (FIXED) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) old[k] = M(0);
+  }
+  M pre[D];
+  M P = M(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const uint32_t sx = Bits<M>::sign_word(v[k]);
+    par ^= sx;
+    M d = Arith<M>::delta(Arith<M>::clip_abs(v[k], l_max, inv_l_max));
+    if constexpr (CHECKED) d = col[k] >= 0 ? d : M(0);
+    v[k] = Bits<M>::with_sign(d, sx & kSign);
+    pre[k] = P;
+    P = Arith<M>::oplus(P, d);
+  }
+  if (!store) return;
+  M S = M(0);
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
+    if (!CHECKED || col[k] >= 0) {
+      const M Dk = Arith<M>::oplus(pre[k], S);
+      const M mag = Arith<M>::clipped_mag(Dk, l_max, inv_l_max);
+      const M nv = Bits<M>::copy_sign(mag, par ^ Bits<M>::sign_word(v[k]));
+      st_msg<POL>(msg + k * kLanes, nv);
+      if constexpr (FIXED) {
+        const int32_t dq = __float2int_rn(float(nv) * qscale) - __float2int_rn(float(old[k]) * qscale);
+        if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
+      }
+    }
+    S = Arith<M>::oplus(S, fabs(v[k]));
+  }
+}
+
+// Check row p (degree order) of one tile, by one warp. Rows of exactly DMAX or
+// DMAX - 1 edges take an unchecked body.
+template <typename M, int DMAX, bool FIXED, int POL>
+__device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, uint32_t act, int first_iter,
+                                            M* __restrict__ c2v, const M* __restrict__ lsrc,
+                                            const uint32_t* __restrict__ zt, M l_max, M inv_l_max,
+                                            int32_t* __restrict__ lacc, float qscale) {
+  const int lane = threadIdx.x & 31;
+  const int base = c.slice_base[p];
+  const int deg = c.slice_base[p + 1] - base;
+  const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
+  M* msg = c2v + (int64_t(tile) * c.s_tot + base) * kLanes + lane;  // edge k at msg[k * kLanes]
+  const M* gsrc = lsrc + node0;                                     // node i at gsrc[i * kLanes]
+  int32_t* lacc_lane = FIXED ? lacc + node0 : nullptr;
+  const int* cols = c.slot_col + base;
+  const uint32_t zw = zt[int64_t(tile) * c.m_tot + p];
+  const uint32_t par = ((zw >> lane) & 1u) << 31;
+  const bool store = (act >> lane) & 1u;
+  if (deg == DMAX)
+    cn_row<M, DMAX, FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
+                                       qscale);
+  else if (DMAX > 1 && deg == DMAX - 1)
+    cn_row<M, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max,
+                                                             inv_l_max, lacc_lane, qscale);
+  else
+    cn_row<M, DMAX, FIXED, true, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
+                                      qscale);
+}
+
+// ------------------------------------------------------------- eq. (2)
+
+// Sum of one node's messages, D >= its degree: the slot indices are loaded
+// first, then all gathers are in flight together; the sum runs in stacked-row
+// order (the order of col_slot).
+template <typename M, int D, int POL>
+__device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const M* __restrict__ msg, M sum) {
+  int slot[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) slot[k] = k < d ? __ldg(slots + k) : -1;
+  M g[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) g[k] = slot[k] >= 0 ? ld_msg<POL>(msg + int64_t(slot[k]) * kLanes) : M(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (slot[k] >= 0) sum += g[k];
+  return sum;
+}
+
+// The variable-node update of node `col` of one tile, by one warp: the soft
+// decision L_V = L_P + sum of the node's C2V over all matrices (eq. 2) and the
+// hard decision, whose 32 lanes are one word of xh. Nodes with more than 16
+// edges are summed 16 edges at a time, still in stacked-row order.
+template <typename M, int POL>
+__device__ __forceinline__ void vn_node(const DevCode& c, int tile, int col, uint32_t act,
+                                        const M* __restrict__ c2v, M* __restrict__ lv, const M* __restrict__ lp,
+                                        uint32_t* __restrict__ xh) {
+  const int lane = threadIdx.x & 31;
+  const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
+  const M* msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
+  const int a0 = c.col_ptr[col];
+  const int d = c.col_ptr[col + 1] - a0;
+  const int* slots = c.col_slot + a0;
+  M sum = lp[at];
+  if (d <= 4) sum = vn_sum<M, 4, POL>(slots, d, msg, sum);
+  else if (d <= 8) sum = vn_sum<M, 8, POL>(slots, d, msg, sum);
+  else
+    for (int b = 0; b < d; b += 16) sum = vn_sum<M, 16, POL>(slots + b, d - b, msg, sum);
+  if ((act >> lane) & 1u) lv[at] = sum;
+  const uint32_t hard = __ballot_sync(kFull, sum < M(0));
+  if (lane == 0) {
+    uint32_t* px = xh + int64_t(tile) * c.n + col;
+    const uint32_t prev = ld_state<POL>(px);
+    *px = (prev & ~act) | (hard & act);
+  }
+}
+
+// ------------------------------------------------------- stopping rule
+
+// Rows r0 .. r0 + 31 of one tile, one per thread of a warp: the lanes whose hard
+// decision breaks the row are ORed into fail[tile][l] (l = the row's matrix).
+// The row's columns are all loaded before the decision words are gathered.
+template <int DMAX, int POL>
+__device__ __forceinline__ void syn_rows(const DevCode& c, int tile, int r0, uint32_t act,
+                                         const uint32_t* __restrict__ xh, const uint32_t* __restrict__ zt,
+                                         uint32_t* __restrict__ fail) {
+  const int r = r0 + (threadIdx.x & 31);
+  uint32_t bad = 0;
+  int l = -1;
+  if (r < c.m_tot) {
+    const int base = c.slice_base[r];
+    const int deg = c.slice_base[r + 1] - base;
+    const int* cp = c.slot_col + base;
+    int col[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(cp + k) : -1;
+    const uint32_t* x = xh + int64_t(tile) * c.n;
+    uint32_t p = zt[int64_t(tile) * c.m_tot + r];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (col[k] >= 0) p ^= ld_state<POL>(x + col[k]);
+    bad = p & act;
+    l = c.row_mat[r];
+  }
+  const int l0 = __shfl_sync(kFull, l, 0);
+  if (__all_sync(kFull, l == l0 || l < 0)) {
+    const uint32_t agg = __reduce_or_sync(kFull, bad);
+    if ((threadIdx.x & 31) == 0 && agg && l0 >= 0) atomicOr(&fail[tile * c.u + l0], agg);
+  } else if (bad) {
+    atomicOr(&fail[tile * c.u + l], bad);
+  }
+}
+
+// Retire the lanes of one tile that satisfied every syndrome (or hit max_iter);
+// returns the lanes still decoding.
+__device__ __forceinline__ uint32_t update_tile(int tile, int F, int u, int t, int max_iter, int early_exit,
+                                                uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
+                                                int32_t* __restrict__ iters, uint8_t* __restrict__ success,
+                                                uint8_t* __restrict__ synd_ok) {
+  uint32_t act = __ldcg(active + tile);
+  if (act == 0) return 0;
+  uint32_t anyfail = 0;
+  for (int l = 0; l < u; ++l) anyfail |= __ldcg(fail + tile * u + l);
+  uint32_t done = 0;
+  if (t >= max_iter) done = act;
+  else if (early_exit) done = act & ~anyfail;
+  for (int lane = 0; lane < kLanes; ++lane) {
+    if (!((done >> lane) & 1u)) continue;
+    const int f = tile * kLanes + lane;
+    if (f >= F) continue;
+    iters[f] = t;
+    success[f] = uint8_t(!((anyfail >> lane) & 1u));
+    if (synd_ok)
+      for (int l = 0; l < u; ++l) synd_ok[int64_t(f) * u + l] = uint8_t(!((__ldcg(fail + tile * u + l) >> lane) & 1u));
+  }
+  act &= ~done;
+  active[tile] = act;
+  for (int l = 0; l < u; ++l) fail[tile * u + l] = 0;
+  return act;
+}
+
+}  // namespace dev
+}  // namespace mbp

@@ -3,15 +3,13 @@
 // Device layout of the stacked code [H_1; ...; H_u] (Section 2: u matrices of
 // size m_l x n sharing the n variable nodes):
 //   * stacked row r = row_first[l] + j is row j of H_l (the CSR arrays);
-//   * for the decoder the rows are put in degree order (position p) and grouped
-//     in slices of kSliceRows positions; a slice whose longest row has d edges
-//     owns kSliceRows * d edge "slots", slot slice_base[s] + k * kSliceRows + q
-//     holding edge k of the row at position kSliceRows*s + q (slot_col = -1
-//     where that row is shorter: padding); row_mat/row_local name the matrix and
-//     row of each position;
-//   * every per-edge message array is indexed [tile][slot][lane]: kLanes frames
-//     ("lanes") are interleaved so that one edge of kLanes frames is one
-//     contiguous 32-byte (FP32) or 64-byte (FP64) vector;
+//   * for the decoder the rows are put in degree order (position p); the row at
+//     position p owns the edge "slots" slice_base[p] .. slice_base[p+1] - 1,
+//     slot slice_base[p] + k holding its edge k (column slot_col); row_mat and
+//     row_local name the matrix and row of each position;
+//   * every per-edge message array is indexed [tile][slot][lane]: kLanes = 32
+//     frames ("lanes") are interleaved, so that one edge of a tile's frames is
+//     one contiguous 128-byte (FP32) vector;
 //   * col_ptr/col_slot list, for every variable node, the slots of its edges in
 //     stacked-row order (the order in which eq. (2) sums them).
 #pragma once
@@ -25,8 +23,7 @@
 
 namespace mbp {
 
-constexpr int kLanes = 8;       // frames interleaved per tile
-constexpr int kSliceRows = 4;   // rows per slice: one warp = kSliceRows rows x kLanes frames
+constexpr int kLanes = 32;      // frames interleaved per tile (one warp lane each)
 constexpr int kMaxU = 16;
 constexpr int kMaxRowDeg = 64;
 constexpr int kMaxDevices = 64;
@@ -35,22 +32,21 @@ constexpr int kMaxQBits = 24;   // fixed-point accumulation: at most 2^-24 resol
 constexpr int kMinQBits = 12;   // and at least 2^-12
 
 struct DevCode {
-  int32_t n, u, m_tot, n_slices;
+  int32_t n, u, m_tot;
   int32_t max_row_deg;
   int32_t max_col_deg;
   int64_t e_tot, s_tot;
   int32_t m[kMaxU];
   int32_t row_first[kMaxU + 1];
-  const int32_t* slice_base;  // [n_slices + 1]
+  const int32_t* slice_base;  // [m_tot + 1] first slot of each row position
   const int32_t* slot_col;    // [s_tot]
   const int32_t* col_ptr;     // [n + 1]
   const int32_t* col_slot;    // [e_tot]
   const int32_t* row_ptr;     // [m_tot + 1] stacked CSR
   const int32_t* col_idx;     // [e_tot]
   const int32_t* edge_slot;   // [e_tot] stacked CSR edge -> slot
-  const uint8_t* row_mat;     // [m_tot] matrix l of the row in slice position p
-  const int32_t* row_local;   // [m_tot] row index j inside H_l of the row in slice position p
-  const uint8_t* slice_full;  // [n_slices] 1 if every row of the slice has the slice's degree
+  const uint8_t* row_mat;     // [m_tot] matrix l of the row at position p
+  const int32_t* row_local;   // [m_tot] row index j inside H_l of the row at position p
 };
 
 // Per-call decoder state carved out of the caller's workspace.
@@ -60,8 +56,8 @@ struct DevState {
   void* lv;           // [n_tiles][n][kLanes] posterior L_V of eq. (2)
   void* lp;           // [n_tiles][n][kLanes] channel LLR L_P
   int32_t* lacc;      // [n_tiles][n][kLanes] fixed-point sum of C2V per node (FP32 single pass), or NULL
-  uint8_t* xh;        // [n_tiles][n] hard decisions, bit lane
-  uint8_t* zt;        // [n_tiles][m_tot] syndrome bits, bit lane
+  uint32_t* xh;       // [n_tiles][n] hard decisions, bit lane
+  uint32_t* zt;       // [n_tiles][m_tot] syndrome bits, bit lane
   uint32_t* active;   // [n_tiles] lanes still decoding
   uint32_t* fail;     // [n_tiles][u] lanes whose hard decision violates some check of H_l
   double* llr_mag;    // [F] ln((1 - e)/e) for the BSC entry points
@@ -128,5 +124,17 @@ cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtyp
                               cudaStream_t s);
 // address of the library's fixed device scratch on the current device (mbp_decode_bsc_static)
 int static_scratch(void** ptr);
+
+// the iteration schedules (mbp_stream.cu, mbp_resident.cu), for M = float or double
+template <typename M>
+int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
+                      float inv_qscale, cudaStream_t s);
+template <typename M>
+int resident_group(const DevCode& c, int n_tiles);
+template <typename M>
+cudaError_t launch_resident_any(const DevCode& c, const DevState& st, const DecodeArgs& a, int G, double l_max,
+                                cudaStream_t s);
+size_t resident_ctl_bytes();
+int resident_error(const void* ctl_host);
 
 }  // namespace mbp

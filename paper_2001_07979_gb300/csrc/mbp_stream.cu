@@ -1,0 +1,202 @@
+// The streaming schedule of libmbp: per iteration (Section 3A, Algorithm 1,
+// flooding over all u matrices), kernels over every tile that still has
+// unfinished frames:
+//   cn_kernel      eq. (6) for every check of every matrix, on V2C = clip(L_V - C2V)
+//   vn_kernel      eq. (2): L_V = L_P + sum of the node's C2V over all u matrices,
+//                  and the hard decision
+//   syn_kernel     the stopping rule H_l x_hat = z^l, per frame and matrix
+//   update_kernel  retire the frames that satisfied it (or ran out of iterations)
+// and the host reads the number of tiles still decoding after each stopping test.
+#include <cmath>
+#include <cstdio>
+
+#include "mbp_device.cuh"
+
+namespace mbp {
+namespace {
+
+using namespace dev;
+
+inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
+
+// One warp per (tile, check row): 8 rows per block, tile = blockIdx.y.
+template <typename M, int DMAX, bool FIXED>
+__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter, M* __restrict__ c2v,
+                                                 const M* __restrict__ lsrc, const uint32_t* __restrict__ zt,
+                                                 const uint32_t* __restrict__ active, M l_max,
+                                                 int32_t* __restrict__ lacc, float qscale) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= c.m_tot) return;
+  cn_tile_row<M, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, zt, l_max, M(1) / l_max, lacc,
+                                          qscale);
+}
+
+// One warp per (tile, variable node): 8 nodes per block.
+template <typename M>
+__global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __restrict__ c2v, M* __restrict__ lv,
+                                                 const M* __restrict__ lp, uint32_t* __restrict__ xh,
+                                                 const uint32_t* __restrict__ active) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (col >= c.n) return;
+  vn_node<M, kPolStream>(c, tile, col, act, c2v, lv, lp, xh);
+}
+
+// L_V = L_P + lacc / qscale and the hard decision, for the fixed-point single
+// pass. One warp per (tile, variable node).
+template <typename M>
+__global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const int32_t* __restrict__ lacc,
+                                                       M* __restrict__ lv, const M* __restrict__ lp,
+                                                       uint32_t* __restrict__ xh, const uint32_t* __restrict__ active,
+                                                       float inv_qscale) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (col >= c.n) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
+  const M sum = lp[at] + M(float(lacc[at]) * inv_qscale);
+  if ((act >> lane) & 1u) lv[at] = sum;
+  const uint32_t hard = __ballot_sync(kFull, sum < M(0));
+  if (lane == 0) {
+    uint32_t* px = xh + int64_t(tile) * c.n + col;
+    *px = (*px & ~act) | (hard & act);
+  }
+}
+
+// One thread per (tile, check row).
+template <int DMAX>
+__global__ void __launch_bounds__(256) syn_kernel(const DevCode c, const uint32_t* __restrict__ xh,
+                                                  const uint32_t* __restrict__ zt,
+                                                  const uint32_t* __restrict__ active, uint32_t* __restrict__ fail) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  syn_rows<DMAX, kPolStream>(c, tile, blockIdx.x * blockDim.x + (threadIdx.x & ~31), act, xh, zt, fail);
+}
+
+// One thread per tile.
+__global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, int early_exit,
+                              uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
+                              int32_t* __restrict__ iters, uint8_t* __restrict__ success,
+                              uint8_t* __restrict__ synd_ok, int32_t* __restrict__ counters) {
+  const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tile >= n_tiles) return;
+  if (update_tile(tile, F, u, t, max_iter, early_exit, active, fail, iters, success, synd_ok))
+    atomicAdd(&counters[0], 1);
+}
+
+template <typename M, int DMAX, bool FIXED>
+void launch_cn(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale, cudaStream_t s) {
+  const dim3 grid(blocks_for(c.m_tot, 8), st.n_tiles);
+  cn_kernel<M, DMAX, FIXED><<<grid, 256, 0, s>>>(c, first_iter, static_cast<M*>(st.c2v),
+                                                 static_cast<const M*>(first_iter ? st.lp : st.lv), st.zt, st.active,
+                                                 M(l_max), st.lacc, qscale);
+}
+
+// Unroll bound at or one above the largest check degree (the last two degrees run without per-edge tests).
+template <typename M, bool FIXED>
+void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale,
+                   cudaStream_t s) {
+  const int d = c.max_row_deg;
+#define MBP_CN(D) launch_cn<M, D, FIXED>(c, st, first_iter, l_max, qscale, s)
+  if constexpr (sizeof(M) == 4 && !FIXED) {
+    if (d <= 4) MBP_CN(4);
+    else if (d <= 6) MBP_CN(6);
+    else if (d <= 8) MBP_CN(8);
+    else if (d <= 10) MBP_CN(10);
+    else if (d <= 12) MBP_CN(12);
+    else if (d <= 14) MBP_CN(14);
+    else if (d <= 16) MBP_CN(16);
+    else if (d <= 18) MBP_CN(18);
+    else if (d <= 20) MBP_CN(20);
+    else if (d <= 22) MBP_CN(22);
+    else if (d <= 24) MBP_CN(24);
+    else if (d <= 32) MBP_CN(32);
+    else MBP_CN(64);
+  } else {
+    if (d <= 8) MBP_CN(8);
+    else if (d <= 16) MBP_CN(16);
+    else if (d <= 32) MBP_CN(32);
+    else MBP_CN(64);
+  }
+#undef MBP_CN
+}
+
+}  // namespace
+
+template <typename M>
+int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
+                      float inv_qscale, cudaStream_t s) {
+  cudaError_t e;
+#define CK(call, what) \
+  if ((e = (call)) != cudaSuccess) return cuda_error(e, what)
+#define CKL(what) CK(cudaGetLastError(), what)
+  const int F = st.F, NT = st.n_tiles;
+  const dim3 syn_grid(blocks_for(c.m_tot, 256), NT);
+  const dim3 node_grid(blocks_for(c.n, 8), NT);
+  int32_t host_ctr[1];
+  auto stop_check = [&](int t, int* left) -> int {
+    prof_begin(MBP_KERNEL_SYNDROME, s);
+    if (c.max_row_deg <= 8) syn_kernel<8><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    else if (c.max_row_deg <= 16) syn_kernel<16><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    else if (c.max_row_deg <= 32) syn_kernel<32><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    else syn_kernel<kMaxRowDeg><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    CKL("syn_kernel");
+    prof_end(MBP_KERNEL_SYNDROME, s, 1);
+    CK(cudaMemsetAsync(st.counters, 0, sizeof(int32_t), s), "clear counter");
+    prof_begin(MBP_KERNEL_RETIRE, s);
+    update_kernel<<<blocks_for(NT, 128), 128, 0, s>>>(F, NT, c.u, t, a.max_iter, a.early_exit, st.active, st.fail,
+                                                       a.iters, a.success, a.synd_ok, st.counters);
+    CKL("update_kernel");
+    prof_end(MBP_KERNEL_RETIRE, s, 1);
+    CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read counter");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *left = host_ctr[0];
+    return MBP_OK;
+  };
+  int left = NT;
+  int rc;
+  if (a.early_exit || a.max_iter == 0) {
+    if ((rc = stop_check(0, &left))) return rc;
+  }
+  for (int t = 1; t <= a.max_iter && left > 0; ++t) {
+    prof_begin(MBP_KERNEL_CHECK, s);
+    if constexpr (sizeof(M) == 4) {
+      if (fixed) launch_cn_any<M, true>(c, st, t == 1, l_max, qscale, s);
+      else launch_cn_any<M, false>(c, st, t == 1, l_max, qscale, s);
+    } else {
+      launch_cn_any<M, false>(c, st, t == 1, l_max, qscale, s);
+    }
+    CKL("cn_kernel");
+    prof_end(MBP_KERNEL_CHECK, s, 1);
+    prof_begin(MBP_KERNEL_VARIABLE, s);
+    if (fixed)
+      finalize_kernel<M><<<node_grid, 256, 0, s>>>(c, st.lacc, static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
+                                                   st.xh, st.active, inv_qscale);
+    else
+      vn_kernel<M><<<node_grid, 256, 0, s>>>(c, static_cast<const M*>(st.c2v), static_cast<M*>(st.lv),
+                                             static_cast<const M*>(st.lp), st.xh, st.active);
+    CKL("vn_kernel");
+    prof_end(MBP_KERNEL_VARIABLE, s, 1);
+    if (a.early_exit || t == a.max_iter) {
+      if ((rc = stop_check(t, &left))) return rc;
+    }
+  }
+#undef CKL
+#undef CK
+  return MBP_OK;
+}
+
+template int stream_iterations<float>(const DevCode&, DevState&, const DecodeArgs&, bool, double, float, float,
+                                      cudaStream_t);
+template int stream_iterations<double>(const DevCode&, DevState&, const DecodeArgs&, bool, double, float, float,
+                                       cudaStream_t);
+
+}  // namespace mbp

@@ -144,9 +144,9 @@ def test_rate05_n1024_u2_qber3(mbp, mode):
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("t", [1, 2, 3, 4, 5])
 def test_messages_within_tolerance_first_iterations(mbp, mode, t):
-    """C2V and L_V after t flooding iterations (no early exit), 13 frames = 2 tiles with a ragged tail."""
+    """C2V and L_V after t flooding iterations (no early exit), 45 frames = 2 tiles of 32 with a ragged tail."""
     msg64 = mode.startswith("f64")
-    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 13, 0.05)
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 45, 0.05)
     codes, out, ref = _decode_both(mbp, w, t, msg64, early_exit=False, want_lv=True, mode=mode)
     tol = TOL_F64 if msg64 else TOL_F32
     ref_c2v = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, t, early_exit=False, want_c2v=True)["c2v"]
