@@ -58,6 +58,8 @@ def parse():
                    help="eq. (2) accumulation: fixed-point single pass or float second pass")
     p.add_argument("--schedule", default="auto", choices=["auto", "streaming", "resident"],
                    help="kernels per iteration, or one cooperative launch keeping tile groups in L2")
+    p.add_argument("--msg-dtype", default="f32", choices=["f32", "f16", "bf16"],
+                   help="message storage: FP32, or FP16/BF16 with FP32 arithmetic")
     return p.parse_args()
 
 
@@ -250,14 +252,16 @@ def run_gb300(args):
     yd = torch.from_numpy(y.view(np.int32)).to(dev)
     ed = torch.from_numpy(e).to(dev)
     zd = mbp.mbp_syndrome(codes, xd)  # Alice's side, untimed
-    ws = torch.empty(mbp.mbp_decode_workspace_size(codes, F, mbp.MSG_F32), dtype=torch.uint8, device=dev)
+    msg = {"f32": mbp.MSG_F32, "f16": mbp.MSG_F16, "bf16": mbp.MSG_BF16}[args.msg_dtype]
+    msg_bytes = {"f32": 4, "f16": 2, "bf16": 2}[args.msg_dtype]
+    ws = torch.empty(mbp.mbp_decode_workspace_size(codes, F, msg), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     acc = {"auto": mbp.ACC_AUTO, "float": mbp.ACC_FLOAT, "fixed": mbp.ACC_FIXED}[args.accumulate]
     sched = {"auto": mbp.SCHED_AUTO, "streaming": mbp.SCHED_STREAMING, "resident": mbp.SCHED_RESIDENT}[args.schedule]
 
     def step():
-        return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=mbp.MSG_F32, l_max=L_MAX, workspace=ws,
+        return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=msg, l_max=L_MAX, workspace=ws,
                                   accumulate=acc, schedule=sched)
 
     for _ in range(max(args.warmup, 3)):
@@ -298,12 +302,11 @@ def run_gb300(args):
     outh = dict(x_hat_bits=torch.empty((F, Wn), dtype=torch.int32).pin_memory(),
                 iters=torch.empty(F, dtype=torch.int32).pin_memory(),
                 success=torch.empty(F, dtype=torch.uint8).pin_memory())
-    wsh = torch.empty(mbp.mbp_decode_workspace_size(codes, F, mbp.MSG_F32, host_io=True), dtype=torch.uint8,
-                      device=dev)
+    wsh = torch.empty(mbp.mbp_decode_workspace_size(codes, F, msg, host_io=True), dtype=torch.uint8, device=dev)
 
     def step_e2e():
-        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, l_max=L_MAX, workspace=wsh, out=outh, accumulate=acc,
-                                schedule=sched)
+        mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, msg_dtype=msg, l_max=L_MAX, workspace=wsh, out=outh,
+                                accumulate=acc, schedule=sched)
 
     for _ in range(2):
         step_e2e()
@@ -328,7 +331,7 @@ def run_gb300(args):
 
     # roofline of the dominant kernel: algorithmic bytes of the frame-iterations it ran / its event time
     e_tot = codes.edges
-    b_check, b_path = algorithmic_bytes(iters, N, e_tot)  # one step
+    b_check, b_path = algorithmic_bytes(iters, N, e_tot, msg_bytes)  # one step
     peak, peak_src = load_peaks()
     dominant = max(prof, key=lambda k: prof[k][1])
     launches = int(sum(v[0] for v in prof.values()))
@@ -351,7 +354,8 @@ def run_gb300(args):
         result = {
             "metric": METRIC, "value": value, "unit": "Mbps", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": args.msg_dtype if args.msg_dtype == "f32" else f"{args.msg_dtype}+f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames_per_gpu": F, "n": N, "m_per_matrix": M, "u": U,
                        "edges": e_tot, "qber": QBER, "max_iter": MAX_ITER, "l_max": L_MAX,
                        "mean_iterations": float(iters.mean()), "max_iterations": int(iters.max()),

@@ -50,15 +50,22 @@ enum {
   MBP_EUNSUPPORTED = 5  /* valid input outside this build's limits (e.g. a check of degree > 64) */
 };
 
-/* message storage precision of the decoder */
-enum { MBP_MSG_F32 = 0, MBP_MSG_F64 = 1 };
+/*
+ * Message storage precision of the decoder. F32 and F64 compute in the
+ * precision they store. F16 and BF16 store every check-to-variable message
+ * rounded to IEEE binary16 / bfloat16 (round to nearest even) and compute the
+ * check-node update, the posteriors and eq. (2) in FP32; their results differ
+ * from F32 by that rounding (relative 2^-11 / 2^-8 per stored message). The
+ * LLR inputs and soft outputs of F16 and BF16 are float.
+ */
+enum { MBP_MSG_F32 = 0, MBP_MSG_F64 = 1, MBP_MSG_F16 = 2, MBP_MSG_BF16 = 3 };
 
 /*
  * How the soft decision of eq. (2), L_V = L_P + sum of the node's C2V over all
  * u matrices, is accumulated:
  *  MBP_ACC_FLOAT  a second pass per iteration sums the node's messages in
  *                 floating point, in stacked-row order (H_1's checks first);
- *  MBP_ACC_FIXED  FP32 only: the check-node pass adds every message's change,
+ *  MBP_ACC_FIXED  MBP_MSG_F32 only: the check-node pass adds every message's change,
  *                 rounded to a multiple of 2^-q, to a 32-bit integer sum per
  *                 node, so each message is read once per iteration. q is the
  *                 largest value <= 24 with (max node degree) x l_max x 2^q < 2^31
@@ -98,7 +105,7 @@ typedef struct {
 typedef struct mbp_codes mbp_codes;
 
 typedef struct {
-  int32_t msg_dtype;      /* MBP_MSG_F32 (default) or MBP_MSG_F64 */
+  int32_t msg_dtype;      /* MBP_MSG_F32 (default), MBP_MSG_F64, MBP_MSG_F16 or MBP_MSG_BF16 */
   int32_t early_exit;     /* 1 (default): each frame stops at its first iteration whose hard
                              decision satisfies every syndrome, tested before iteration 1 too;
                              0: every frame runs exactly max_iter iterations */
@@ -110,7 +117,7 @@ typedef struct {
                              decode call (see mbp_export_c2v) until the next call that uses it */
   size_t workspace_bytes;
   void* soft_out;         /* optional device [F][n] posterior L_V of eq. (2) at the last iteration
-                             each frame ran (float for F32, double for F64); NULL to skip */
+                             each frame ran (double for F64, float for the others); NULL to skip */
   uint8_t* synd_ok;       /* optional device [F][u]: 1 where H_l x_hat = z^l for the output bits */
   int32_t accumulate;     /* MBP_ACC_AUTO (default), MBP_ACC_FLOAT or MBP_ACC_FIXED */
   int32_t schedule;       /* MBP_SCHED_AUTO (default), MBP_SCHED_STREAMING or MBP_SCHED_RESIDENT */
@@ -168,7 +175,7 @@ int mbp_decode_workspace_size(const mbp_codes* codes, int F, const mbp_opts* opt
  *   iteration, every variable forms L_V = L_P + sum over all matrices of its
  *   C2V (eq. 2), and the hard decision is bit = [L_V < 0]; the stopping rule
  *   is H_l x_hat = z^l for every l.
- * llr:     device [F][n], float for MBP_MSG_F32, double for MBP_MSG_F64.
+ * llr:     device [F][n], double for MBP_MSG_F64, float for the others.
  * z_bits:  device [u][F][ceil(m_l/32)] (Alice's syndromes).
  * max_iter >= 0.
  * Outputs (device): x_hat_bits [F][ceil(n/32)]; iters [F] = iterations run
@@ -204,8 +211,8 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
 /*
  * Copy the check-to-variable messages of one frame, as left in the workspace
  * by the last decode with these opts, to c2v_out (device, [edges] in stacked
- * CSR order: H_1's edges row by row, then H_2's, ...; float or double by
- * msg_dtype). Meant for inspection after an early_exit = 0 decode, where every
+ * CSR order: H_1's edges row by row, then H_2's, ...; double for F64, float
+ * for the others). Meant for inspection after an early_exit = 0 decode, where every
  * frame ran max_iter >= 1 iterations.
  */
 int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int frame, void* c2v_out,

@@ -23,14 +23,14 @@ import torch
 from ._build import LIB, build, up_to_date
 
 __all__ = [
-    "build", "library_path", "MBPError", "Codes", "MSG_F32", "MSG_F64", "ACC_AUTO", "ACC_FLOAT", "ACC_FIXED",
+    "build", "library_path", "MBPError", "Codes", "MSG_F32", "MSG_F64", "MSG_F16", "MSG_BF16", "ACC_AUTO", "ACC_FLOAT", "ACC_FIXED",
     "SCHED_AUTO", "SCHED_STREAMING", "SCHED_RESIDENT",
     "mbp_create_codes", "mbp_destroy_codes", "mbp_syndrome", "mbp_bsc_llr", "mbp_decode_workspace_size",
     "mbp_decode_batch", "mbp_decode_bsc", "mbp_decode_bsc_host", "mbp_export_c2v", "mbp_version",
     "split_syndromes", "join_syndromes", "mbp_profile_enable", "mbp_profile_get", "KERNEL_FAMILIES",
 ]
 
-MSG_F32, MSG_F64 = 0, 1
+MSG_F32, MSG_F64, MSG_F16, MSG_BF16 = 0, 1, 2, 3
 ACC_AUTO, ACC_FLOAT, ACC_FIXED = 0, 1, 2
 SCHED_AUTO, SCHED_STREAMING, SCHED_RESIDENT = 0, 1, 2
 _STATUS = {0: "MBP_OK", 1: "MBP_EINVAL", 2: "MBP_ENOMEM", 3: "MBP_ECUDA", 4: "MBP_ETIMEOUT", 5: "MBP_EUNSUPPORTED"}
@@ -273,12 +273,15 @@ def _decode(entry, codes, F, inputs, z_bits, max_iter, msg_dtype, l_max, early_e
 def mbp_decode_batch(codes: Codes, llr: torch.Tensor, z_bits: torch.Tensor, max_iter: int, *, l_max: float = 20.0,
                      early_exit: bool = True, validate: bool = False, want_soft: bool = False,
                      want_synd: bool = False, workspace: torch.Tensor | None = None, stream=None,
-                     accumulate: int = ACC_AUTO, schedule: int = SCHED_AUTO) -> dict:
-    """Decode F frames from channel LLRs (float32 -> FP32 messages, float64 -> FP64 messages)."""
+                     accumulate: int = ACC_AUTO, schedule: int = SCHED_AUTO, msg_dtype: int | None = None) -> dict:
+    """Decode F frames from channel LLRs: float64 LLRs decode with FP64 messages, float32 LLRs with FP32
+    messages unless msg_dtype asks for MSG_F16 or MSG_BF16 storage."""
     x = llr.contiguous()
-    msg = MSG_F64 if x.dtype == torch.float64 else MSG_F32
     if x.dtype not in (torch.float32, torch.float64):
         raise TypeError("llr must be float32 or float64")
+    msg = MSG_F64 if x.dtype == torch.float64 else (MSG_F32 if msg_dtype is None else msg_dtype)
+    if (msg == MSG_F64) != (x.dtype == torch.float64):
+        raise TypeError("FP64 messages take float64 LLRs; the other storage types take float32")
     return _decode(_load().mbp_decode_batch, codes, x.shape[0], [x], z_bits, max_iter, msg, l_max, early_exit,
                    validate, want_soft, want_synd, workspace, x.device, stream, accumulate, schedule)
 

@@ -130,7 +130,9 @@ namespace {
 
 int validate_opts(const mbp_opts* o) {
   REQUIRE(o, "opts is NULL");
-  REQUIRE(o->msg_dtype == MBP_MSG_F32 || o->msg_dtype == MBP_MSG_F64, "unknown msg_dtype %d", o->msg_dtype);
+  REQUIRE(o->msg_dtype == MBP_MSG_F32 || o->msg_dtype == MBP_MSG_F64 || o->msg_dtype == MBP_MSG_F16 ||
+              o->msg_dtype == MBP_MSG_BF16,
+          "unknown msg_dtype %d", o->msg_dtype);
   REQUIRE(o->early_exit == 0 || o->early_exit == 1, "early_exit must be 0 or 1");
   REQUIRE(std::isfinite(o->l_max) && o->l_max > 0, "l_max must be finite and > 0");
   REQUIRE(o->accumulate == MBP_ACC_AUTO || o->accumulate == MBP_ACC_FLOAT || o->accumulate == MBP_ACC_FIXED,

@@ -19,6 +19,8 @@
 // MUFU operations in, two out (exp + reciprocal, reciprocal + log).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -115,6 +117,36 @@ struct Bits<double> {
   }
 };
 
+// Stored message type S and arithmetic type M: FP32 and FP64 store what they
+// compute; FP16 and BF16 store rounded copies of FP32 messages (round to
+// nearest even) and widen them on load.
+template <typename S>
+struct Store;
+
+template <>
+struct Store<float> {
+  static __device__ __forceinline__ float widen(float v) { return v; }
+  static __device__ __forceinline__ float narrow(float v) { return v; }
+};
+
+template <>
+struct Store<double> {
+  static __device__ __forceinline__ double widen(double v) { return v; }
+  static __device__ __forceinline__ double narrow(double v) { return v; }
+};
+
+template <>
+struct Store<__half> {
+  static __device__ __forceinline__ float widen(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half narrow(float v) { return __float2half_rn(v); }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+  static __device__ __forceinline__ float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 narrow(float v) { return __float2bfloat16_rn(v); }
+};
+
 // Memory policies.
 //  kPolStream:   streaming kernels, which only read data written by earlier
 //                launches: posterior through the read-only path, messages
@@ -156,9 +188,9 @@ __device__ __forceinline__ void st_msg(T* p, T v) {
 // node (a 32-bit red.global.add in L2). Integer addition is associative, so
 // the accumulated sum sum_e q(C2V_e) is exact and independent of the order of
 // the atomics; finalize_kernel turns it into L_V.
-template <typename M, int D, bool FIXED, bool CHECKED, int POL>
+template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL>
 __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, const M* __restrict__ gsrc,
-                                       M* __restrict__ msg, int first_iter, uint32_t par, bool store, M l_max,
+                                       S* __restrict__ msg, int first_iter, uint32_t par, bool store, M l_max,
                                        M inv_l_max, int32_t* __restrict__ lacc, float qscale) {
   int col[D];
 #pragma unroll
@@ -170,7 +202,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const M o = (!CHECKED || col[k] >= 0) ? ld_msg<POL>(msg + k * kLanes) : M(0);
+      const M o = (!CHECKED || col[k] >= 0) ? M(Store<S>::widen(ld_msg<POL>(msg + k * kLanes))) : M(0);
       if constexpr (FIXED) old[k] = o;
       v[k] -= o;
     }
@@ -191,35 +223,35 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
     P = Arith<M>::oplus(P, d);
   }
   if (!store) return;
-  M S = M(0);
+  M suf = M(0);
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
     if (!CHECKED || col[k] >= 0) {
-      const M Dk = Arith<M>::oplus(pre[k], S);
+      const M Dk = Arith<M>::oplus(pre[k], suf);
       const M mag = Arith<M>::clipped_mag(Dk, l_max, inv_l_max);
       const M nv = Bits<M>::copy_sign(mag, par ^ Bits<M>::sign_word(v[k]));
-      st_msg<POL>(msg + k * kLanes, nv);
+      st_msg<POL>(msg + k * kLanes, Store<S>::narrow(nv));
       if constexpr (FIXED) {
         const int32_t dq = __float2int_rn(float(nv) * qscale) - __float2int_rn(float(old[k]) * qscale);
         if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
       }
     }
-    S = Arith<M>::oplus(S, fabs(v[k]));
+    suf = Arith<M>::oplus(suf, fabs(v[k]));
   }
 }
 
 // Check row p (degree order) of one tile, by one warp. Rows of exactly DMAX or
 // DMAX - 1 edges take an unchecked body.
-template <typename M, int DMAX, bool FIXED, int POL>
+template <typename M, typename S, int DMAX, bool FIXED, int POL>
 __device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, uint32_t act, int first_iter,
-                                            M* __restrict__ c2v, const M* __restrict__ lsrc,
+                                            S* __restrict__ c2v, const M* __restrict__ lsrc,
                                             const uint32_t* __restrict__ zt, M l_max, M inv_l_max,
                                             int32_t* __restrict__ lacc, float qscale) {
   const int lane = threadIdx.x & 31;
   const int base = c.slice_base[p];
   const int deg = c.slice_base[p + 1] - base;
   const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
-  M* msg = c2v + (int64_t(tile) * c.s_tot + base) * kLanes + lane;  // edge k at msg[k * kLanes]
+  S* msg = c2v + (int64_t(tile) * c.s_tot + base) * kLanes + lane;  // edge k at msg[k * kLanes]
   const M* gsrc = lsrc + node0;                                     // node i at gsrc[i * kLanes]
   int32_t* lacc_lane = FIXED ? lacc + node0 : nullptr;
   const int* cols = c.slot_col + base;
@@ -227,13 +259,13 @@ __device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, u
   const uint32_t par = ((zw >> lane) & 1u) << 31;
   const bool store = (act >> lane) & 1u;
   if (deg == DMAX)
-    cn_row<M, DMAX, FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
+    cn_row<M, S, DMAX, FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
                                        qscale);
   else if (DMAX > 1 && deg == DMAX - 1)
-    cn_row<M, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max,
+    cn_row<M, S, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max,
                                                              inv_l_max, lacc_lane, qscale);
   else
-    cn_row<M, DMAX, FIXED, true, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
+    cn_row<M, S, DMAX, FIXED, true, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
                                       qscale);
 }
 
@@ -242,14 +274,15 @@ __device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, u
 // Sum of one node's messages, D >= its degree: the slot indices are loaded
 // first, then all gathers are in flight together; the sum runs in stacked-row
 // order (the order of col_slot).
-template <typename M, int D, int POL>
-__device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const M* __restrict__ msg, M sum) {
+template <typename M, typename S, int D, int POL>
+__device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const S* __restrict__ msg, M sum) {
   int slot[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) slot[k] = k < d ? __ldg(slots + k) : -1;
   M g[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) g[k] = slot[k] >= 0 ? ld_msg<POL>(msg + int64_t(slot[k]) * kLanes) : M(0);
+  for (int k = 0; k < D; ++k)
+    g[k] = slot[k] >= 0 ? M(Store<S>::widen(ld_msg<POL>(msg + int64_t(slot[k]) * kLanes))) : M(0);
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (slot[k] >= 0) sum += g[k];
@@ -260,21 +293,21 @@ __device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const 
 // decision L_V = L_P + sum of the node's C2V over all matrices (eq. 2) and the
 // hard decision, whose 32 lanes are one word of xh. Nodes with more than 16
 // edges are summed 16 edges at a time, still in stacked-row order.
-template <typename M, int POL>
+template <typename M, typename S, int POL>
 __device__ __forceinline__ void vn_node(const DevCode& c, int tile, int col, uint32_t act,
-                                        const M* __restrict__ c2v, M* __restrict__ lv, const M* __restrict__ lp,
+                                        const S* __restrict__ c2v, M* __restrict__ lv, const M* __restrict__ lp,
                                         uint32_t* __restrict__ xh) {
   const int lane = threadIdx.x & 31;
   const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
-  const M* msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
+  const S* msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
   const int a0 = c.col_ptr[col];
   const int d = c.col_ptr[col + 1] - a0;
   const int* slots = c.col_slot + a0;
   M sum = lp[at];
-  if (d <= 4) sum = vn_sum<M, 4, POL>(slots, d, msg, sum);
-  else if (d <= 8) sum = vn_sum<M, 8, POL>(slots, d, msg, sum);
+  if (d <= 4) sum = vn_sum<M, S, 4, POL>(slots, d, msg, sum);
+  else if (d <= 8) sum = vn_sum<M, S, 8, POL>(slots, d, msg, sum);
   else
-    for (int b = 0; b < d; b += 16) sum = vn_sum<M, 16, POL>(slots + b, d - b, msg, sum);
+    for (int b = 0; b < d; b += 16) sum = vn_sum<M, S, 16, POL>(slots + b, d - b, msg, sum);
   if ((act >> lane) & 1u) lv[at] = sum;
   const uint32_t hard = __ballot_sync(kFull, sum < M(0));
   if (lane == 0) {

@@ -14,6 +14,8 @@
 //     stacked-row order (the order in which eq. (2) sums them).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -125,8 +127,9 @@ cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtyp
 // address of the library's fixed device scratch on the current device (mbp_decode_bsc_static)
 int static_scratch(void** ptr);
 
-// the iteration schedules (mbp_stream.cu, mbp_resident.cu), for M = float or double
-template <typename M>
+// the iteration schedules: streaming (mbp_stream_<type>.cu) for arithmetic type M and stored message type S
+// (float/float, double/double, float/__half, float/__nv_bfloat16), resident (mbp_resident.cu, M = S)
+template <typename M, typename S>
 int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
                       float inv_qscale, cudaStream_t s);
 template <typename M>

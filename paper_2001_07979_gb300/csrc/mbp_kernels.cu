@@ -168,17 +168,17 @@ __global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv
   out[idx] = M((iters[f] == 0 ? lp[at] : lv[at]) * Arith<M>::kToLLR);
 }
 
-template <typename M>
-__global__ void export_c2v_kernel(const DevCode c, const M* __restrict__ c2v, int frame, M* __restrict__ out) {
+template <typename M, typename S>
+__global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, int frame, M* __restrict__ out) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= c.e_tot) return;
   const int tile = frame / kLanes, lane = frame % kLanes;
-  out[e] = M(c2v[(int64_t(tile) * c.s_tot + c.edge_slot[e]) * kLanes + lane] * Arith<M>::kToLLR);
+  out[e] = M(Store<S>::widen(c2v[(int64_t(tile) * c.s_tot + c.edge_slot[e]) * kLanes + lane])) * Arith<M>::kToLLR;
 }
 
 // ------------------------------------------------------------- driver
 
-template <typename M>
+template <typename M, typename S>
 int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s) {
   cudaError_t e;
 #define CK(call, what) \
@@ -192,10 +192,10 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
     const double bound = double(c.max_col_deg > 0 ? c.max_col_deg : 1) * l_max;
     while (qbits < kMaxQBits && bound * std::ldexp(1.0, qbits + 1) < 2147483647.0) ++qbits;
   }
-  const bool fixed_ok = sizeof(M) == 4 && st.lacc && qbits >= kMinQBits;
+  const bool fixed_ok = sizeof(M) == 4 && sizeof(S) == 4 && st.lacc && qbits >= kMinQBits;
   if (a.accumulate == MBP_ACC_FIXED && !fixed_ok)
-    return set_error(MBP_EUNSUPPORTED, "fixed-point accumulation needs FP32 messages and max node degree x l_max"
-                                       " <= 2^%d", 31 - kMinQBits);
+    return set_error(MBP_EUNSUPPORTED, "fixed-point accumulation needs FP32 message storage and max node degree x"
+                                       " l_max <= 2^%d", 31 - kMinQBits);
   const bool fixed = fixed_ok && a.accumulate == MBP_ACC_FIXED;
   const float qscale = float(std::ldexp(1.0, qbits)), inv_qscale = float(std::ldexp(1.0, -qbits));
   CK(cudaMemsetAsync(st.counters, 0, 4 * sizeof(int32_t), s), "clear counters");
@@ -221,9 +221,11 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
     if (host_ctr[1]) return set_error(MBP_EINVAL, "llr holds a non-finite value");
   }
   // schedule: resident (one cooperative launch, groups of tiles kept in L2) or streaming (kernels per iteration)
-  const int G = (fixed || a.schedule != MBP_SCHED_RESIDENT) ? 0 : resident_group<M>(c, NT);
+  constexpr bool same_store = sizeof(M) == sizeof(S);
+  const int G = (fixed || !same_store || a.schedule != MBP_SCHED_RESIDENT) ? 0 : resident_group<M>(c, NT);
   if (a.schedule == MBP_SCHED_RESIDENT && G == 0)
     return set_error(MBP_EUNSUPPORTED, fixed ? "the resident schedule accumulates in floating point only"
+                                       : !same_store ? "the resident schedule stores FP32 or FP64 messages only"
                                              : "one tile of this code does not fit the resident schedule's L2 budget");
   if (G > 0) {
     CK(cudaMemsetAsync(st.ctl, 0, resident_ctl_bytes(), s), "clear resident control");
@@ -235,7 +237,7 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (resident_error(ctl_h)) return set_error(MBP_ETIMEOUT, "a grid barrier of the resident schedule timed out");
   } else {
-    const int rc = stream_iterations<M>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
+    const int rc = stream_iterations<M, S>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
     if (rc) return rc;
   }
   const int wn = (c.n + 31) >> 5;
@@ -255,7 +257,11 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
 
 constexpr int kRegions = 17;
 
-size_t msg_size(int msg_dtype) { return msg_dtype == MBP_MSG_F64 ? 8 : 4; }
+// bytes of one stored message and of one posterior / channel value
+size_t msg_size(int msg_dtype) {
+  return msg_dtype == MBP_MSG_F64 ? 8 : (msg_dtype == MBP_MSG_F32 ? 4 : 2);
+}
+size_t node_size(int msg_dtype) { return msg_dtype == MBP_MSG_F64 ? 8 : 4; }
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -267,8 +273,8 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
   for (int l = 0; l < c.u; ++l) zw += (size_t(c.m[l]) + 31) / 32;
   const size_t sizes[kRegions] = {
       NT * size_t(c.s_tot) * kLanes * ms,                             // c2v
-      NT * size_t(c.n) * kLanes * ms,                                 // lv
-      NT * size_t(c.n) * kLanes * ms,                                 // lp
+      NT * size_t(c.n) * kLanes * node_size(msg_dtype),               // lv
+      NT * size_t(c.n) * kLanes * node_size(msg_dtype),               // lp
       msg_dtype == MBP_MSG_F32 ? NT * size_t(c.n) * kLanes * 4 : 0,  // lacc
       NT * size_t(c.n) * 4,                                           // xh
       NT * size_t(c.m_tot) * 4,                                       // zt
@@ -348,7 +354,12 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
 
 int decode(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {
   if (st.n_tiles > 65535) return set_error(MBP_EUNSUPPORTED, "F = %d exceeds %d frames per call", st.F, 65535 * kLanes);
-  return msg_dtype == MBP_MSG_F64 ? decode_t<double>(c, st, a, s) : decode_t<float>(c, st, a, s);
+  switch (msg_dtype) {
+    case MBP_MSG_F64: return decode_t<double, double>(c, st, a, s);
+    case MBP_MSG_F16: return decode_t<float, __half>(c, st, a, s);
+    case MBP_MSG_BF16: return decode_t<float, __nv_bfloat16>(c, st, a, s);
+    default: return decode_t<float, float>(c, st, a, s);
+  }
 }
 
 // Device address of g_static_scratch on the current device. Host code only holds
@@ -375,12 +386,19 @@ int static_scratch(void** ptr) {
 cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtype, int frame, void* out,
                               cudaStream_t s) {
   if (c.e_tot == 0) return cudaSuccess;
+  const unsigned grid = blocks_for(c.e_tot, 256);
   if (msg_dtype == MBP_MSG_F64)
-    export_c2v_kernel<double><<<blocks_for(c.e_tot, 256), 256, 0, s>>>(c, static_cast<const double*>(st.c2v), frame,
-                                                                         static_cast<double*>(out));
+    export_c2v_kernel<double, double><<<grid, 256, 0, s>>>(c, static_cast<const double*>(st.c2v), frame,
+                                                            static_cast<double*>(out));
+  else if (msg_dtype == MBP_MSG_F16)
+    export_c2v_kernel<float, __half><<<grid, 256, 0, s>>>(c, static_cast<const __half*>(st.c2v), frame,
+                                                           static_cast<float*>(out));
+  else if (msg_dtype == MBP_MSG_BF16)
+    export_c2v_kernel<float, __nv_bfloat16><<<grid, 256, 0, s>>>(c, static_cast<const __nv_bfloat16*>(st.c2v), frame,
+                                                                  static_cast<float*>(out));
   else
-    export_c2v_kernel<float><<<blocks_for(c.e_tot, 256), 256, 0, s>>>(c, static_cast<const float*>(st.c2v), frame,
-                                                                        static_cast<float*>(out));
+    export_c2v_kernel<float, float><<<grid, 256, 0, s>>>(c, static_cast<const float*>(st.c2v), frame,
+                                                          static_cast<float*>(out));
   return cudaGetLastError();
 }
 

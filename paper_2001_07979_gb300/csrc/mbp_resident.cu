@@ -115,14 +115,14 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
         const int tile = g0 + it / c.m_tot;
         const uint32_t act = __ldcg(active + tile);
         if (act)
-          cn_tile_row<M, DMAX, false, kPolCoherent>(c, tile, it % c.m_tot, act, t == 1, c2v, lsrc, zt, l_max,
+          cn_tile_row<M, M, DMAX, false, kPolCoherent>(c, tile, it % c.m_tot, act, t == 1, c2v, lsrc, zt, l_max,
                                                     inv_l_max, nullptr, 0.f);
       }
       if (!grid_sync(ctl, gen, bc)) return;
       for (int it = gw; it < gt * c.n; it += warps) {
         const int tile = g0 + it / c.n;
         const uint32_t act = __ldcg(active + tile);
-        if (act) vn_node<M, kPolCoherent>(c, tile, it % c.n, act, c2v, lv, lp, xh);
+        if (act) vn_node<M, M, kPolCoherent>(c, tile, it % c.n, act, c2v, lv, lp, xh);
       }
       if (!grid_sync(ctl, gen, bc)) return;
       if (early_exit || t == max_iter) {

@@ -7,21 +7,29 @@
 //   syn_kernel     the stopping rule H_l x_hat = z^l, per frame and matrix
 //   update_kernel  retire the frames that satisfied it (or ran out of iterations)
 // and the host reads the number of tiles still decoding after each stopping test.
+//
+// M is the arithmetic type (float or double), S the stored message type (M
+// itself, or __half / __nv_bfloat16 with M = float). Each (M, S) pair is
+// instantiated in a file of its own (mbp_stream_<type>.cu) so they build in
+// parallel.
+#pragma once
+
 #include <cmath>
 #include <cstdio>
 
 #include "mbp_device.cuh"
 
 namespace mbp {
-namespace {
+namespace {  // every file that includes this keeps its own copies
+namespace stream {
 
 using namespace dev;
 
 inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
 // One warp per (tile, check row): 8 rows per block, tile = blockIdx.y.
-template <typename M, int DMAX, bool FIXED>
-__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter, M* __restrict__ c2v,
+template <typename M, typename S, int DMAX, bool FIXED>
+__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter, S* __restrict__ c2v,
                                                  const M* __restrict__ lsrc, const uint32_t* __restrict__ zt,
                                                  const uint32_t* __restrict__ active, M l_max,
                                                  int32_t* __restrict__ lacc, float qscale) {
@@ -30,13 +38,13 @@ __global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter
   if (act == 0) return;
   const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (p >= c.m_tot) return;
-  cn_tile_row<M, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, zt, l_max, M(1) / l_max, lacc,
+  cn_tile_row<M, S, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, zt, l_max, M(1) / l_max, lacc,
                                           qscale);
 }
 
 // One warp per (tile, variable node): 8 nodes per block.
-template <typename M>
-__global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __restrict__ c2v, M* __restrict__ lv,
+template <typename M, typename S>
+__global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __restrict__ c2v, M* __restrict__ lv,
                                                  const M* __restrict__ lp, uint32_t* __restrict__ xh,
                                                  const uint32_t* __restrict__ active) {
   const int tile = blockIdx.y;
@@ -44,7 +52,7 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const M* __res
   if (act == 0) return;
   const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= c.n) return;
-  vn_node<M, kPolStream>(c, tile, col, act, c2v, lv, lp, xh);
+  vn_node<M, S, kPolStream>(c, tile, col, act, c2v, lv, lp, xh);
 }
 
 // L_V = L_P + lacc / qscale and the hard decision, for the fixed-point single
@@ -92,20 +100,20 @@ __global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, in
     atomicAdd(&counters[0], 1);
 }
 
-template <typename M, int DMAX, bool FIXED>
+template <typename M, typename S, int DMAX, bool FIXED>
 void launch_cn(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale, cudaStream_t s) {
   const dim3 grid(blocks_for(c.m_tot, 8), st.n_tiles);
-  cn_kernel<M, DMAX, FIXED><<<grid, 256, 0, s>>>(c, first_iter, static_cast<M*>(st.c2v),
+  cn_kernel<M, S, DMAX, FIXED><<<grid, 256, 0, s>>>(c, first_iter, static_cast<S*>(st.c2v),
                                                  static_cast<const M*>(first_iter ? st.lp : st.lv), st.zt, st.active,
                                                  M(l_max), st.lacc, qscale);
 }
 
 // Unroll bound at or one above the largest check degree (the last two degrees run without per-edge tests).
-template <typename M, bool FIXED>
+template <typename M, typename S, bool FIXED>
 void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale,
                    cudaStream_t s) {
   const int d = c.max_row_deg;
-#define MBP_CN(D) launch_cn<M, D, FIXED>(c, st, first_iter, l_max, qscale, s)
+#define MBP_CN(D) launch_cn<M, S, D, FIXED>(c, st, first_iter, l_max, qscale, s)
   if constexpr (sizeof(M) == 4 && !FIXED) {
     if (d <= 4) MBP_CN(4);
     else if (d <= 6) MBP_CN(6);
@@ -129,10 +137,8 @@ void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double 
 #undef MBP_CN
 }
 
-}  // namespace
-
-template <typename M>
-int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
+template <typename M, typename S>
+int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
                       float inv_qscale, cudaStream_t s) {
   cudaError_t e;
 #define CK(call, what) \
@@ -168,11 +174,11 @@ int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool 
   }
   for (int t = 1; t <= a.max_iter && left > 0; ++t) {
     prof_begin(MBP_KERNEL_CHECK, s);
-    if constexpr (sizeof(M) == 4) {
-      if (fixed) launch_cn_any<M, true>(c, st, t == 1, l_max, qscale, s);
-      else launch_cn_any<M, false>(c, st, t == 1, l_max, qscale, s);
+    if constexpr (sizeof(M) == 4 && sizeof(S) == 4) {
+      if (fixed) launch_cn_any<M, S, true>(c, st, t == 1, l_max, qscale, s);
+      else launch_cn_any<M, S, false>(c, st, t == 1, l_max, qscale, s);
     } else {
-      launch_cn_any<M, false>(c, st, t == 1, l_max, qscale, s);
+      launch_cn_any<M, S, false>(c, st, t == 1, l_max, qscale, s);
     }
     CKL("cn_kernel");
     prof_end(MBP_KERNEL_CHECK, s, 1);
@@ -181,7 +187,7 @@ int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool 
       finalize_kernel<M><<<node_grid, 256, 0, s>>>(c, st.lacc, static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
                                                    st.xh, st.active, inv_qscale);
     else
-      vn_kernel<M><<<node_grid, 256, 0, s>>>(c, static_cast<const M*>(st.c2v), static_cast<M*>(st.lv),
+      vn_kernel<M, S><<<node_grid, 256, 0, s>>>(c, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv),
                                              static_cast<const M*>(st.lp), st.xh, st.active);
     CKL("vn_kernel");
     prof_end(MBP_KERNEL_VARIABLE, s, 1);
@@ -194,9 +200,6 @@ int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool 
   return MBP_OK;
 }
 
-template int stream_iterations<float>(const DevCode&, DevState&, const DecodeArgs&, bool, double, float, float,
-                                      cudaStream_t);
-template int stream_iterations<double>(const DevCode&, DevState&, const DecodeArgs&, bool, double, float, float,
-                                       cudaStream_t);
-
+}  // namespace stream
+}  // namespace
 }  // namespace mbp

@@ -1,0 +1,12 @@
+// Streaming schedule with __nv_bfloat16 message storage and float arithmetic (see mbp_stream.cuh).
+#include "mbp_stream.cuh"
+
+namespace mbp {
+
+template <>
+int stream_iterations<float, __nv_bfloat16>(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max,
+                                 float qscale, float inv_qscale, cudaStream_t s) {
+  return stream::run<float, __nv_bfloat16>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
+}
+
+}  // namespace mbp

@@ -1,0 +1,12 @@
+// Streaming schedule with double message storage and double arithmetic (see mbp_stream.cuh).
+#include "mbp_stream.cuh"
+
+namespace mbp {
+
+template <>
+int stream_iterations<double, double>(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max,
+                                 float qscale, float inv_qscale, cudaStream_t s) {
+  return stream::run<double, double>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
+}
+
+}  // namespace mbp

@@ -100,7 +100,7 @@ def test_bsc_llr_matches_oracle(mbp):
 
 # ------------------------------------------------------- whole decoder
 
-MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident"]
+MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident", "f16", "bf16"]
 
 
 def mode_args(mbp, mode):
@@ -112,7 +112,25 @@ def mode_args(mbp, mode):
         return dict(msg_dtype=mbp.MSG_F32, accumulate=mbp.ACC_FIXED, schedule=mbp.SCHED_STREAMING)
     if mode == "f64-resident":
         return dict(msg_dtype=mbp.MSG_F64, schedule=mbp.SCHED_RESIDENT)
+    if mode == "f16":
+        return dict(msg_dtype=mbp.MSG_F16)
+    if mode == "bf16":
+        return dict(msg_dtype=mbp.MSG_BF16)
     return dict(msg_dtype=mbp.MSG_F32, schedule=mbp.SCHED_RESIDENT)
+
+
+# Storage rounding of one message (unit roundoff of the stored format times the largest stored magnitude,
+# l_max = 20, in natural-log units): the L_V of a node with d edges can differ from FP32 by d times that after
+# the first iteration. Later iterations carry these differences on; their size is reported, not bounded.
+STORE_ROUNDOFF = {"f16": 2.0 ** -11 * 32.0 * 0.6931471805599453, "bf16": 2.0 ** -8 * 32.0 * 0.6931471805599453}
+
+
+def tolerance(mode, t, max_col_deg):
+    if mode.startswith("f64"):
+        return TOL_F64
+    if mode in STORE_ROUNDOFF:
+        return max_col_deg * STORE_ROUNDOFF[mode] + TOL_F32 if t == 1 else None
+    return TOL_F32
 
 
 def _decode_both(mbp, w, max_iter, msg64, early_exit=True, want_lv=False, threads=8, mode=None):
@@ -137,8 +155,9 @@ def test_rate05_n1024_u2_qber3(mbp, mode):
     _, out, ref = _decode_both(mbp, w, 50, msg64, want_lv=True, mode=mode)
     check_outputs_bit_exact(out, ref, w.n, fp64=msg64)
     assert ref["success"].all()
-    tol = TOL_F64 if msg64 else TOL_F32
-    assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= tol
+    if mode not in STORE_ROUNDOFF:  # converged posteriors run into the clip; F16/BF16 differ by storage rounding
+        tol = TOL_F64 if msg64 else TOL_F32
+        assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= tol
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -148,12 +167,17 @@ def test_messages_within_tolerance_first_iterations(mbp, mode, t):
     msg64 = mode.startswith("f64")
     w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 45, 0.05)
     codes, out, ref = _decode_both(mbp, w, t, msg64, early_exit=False, want_lv=True, mode=mode)
-    tol = TOL_F64 if msg64 else TOL_F32
+    tol = tolerance(mode, t, codes_max_col_deg(w.H))
     ref_c2v = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, t, early_exit=False, want_c2v=True)["c2v"]
-    assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= tol
-    for f in range(w.F):
-        c = mbp.mbp_export_c2v(codes, w.F, out["workspace"], f, mbp.MSG_F64 if msg64 else mbp.MSG_F32)
-        assert np.max(np.abs(c.cpu().numpy() - ref_c2v[f])) <= tol, f
+    err_lv = np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"]))
+    dt = mode_args(mbp, mode)["msg_dtype"]
+    err_c2v = max(np.max(np.abs(mbp.mbp_export_c2v(codes, w.F, out["workspace"], f, dt).cpu().numpy() - ref_c2v[f]))
+                  for f in range(w.F))
+    print(f"{mode} t={t}: max |dL_V| = {err_lv:.3g}, max |dC2V| = {err_c2v:.3g}")
+    if tol is not None:
+        assert err_lv <= tol and err_c2v <= tol
+    else:  # F16/BF16 after the first iteration: reported; sanity bound only
+        assert err_lv <= 10.0 and err_c2v <= 10.0
     assert np.array_equal(out["iters"].cpu().numpy(), np.full(w.F, t))
 
 
@@ -174,7 +198,11 @@ def test_rate07_n65536_first_iterations_fp32(mbp, mode):
             assert np.max(np.abs(c - ref["c2v"][f])) <= TOL_F32
 
 
-@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed", "f32-resident"])
+def codes_max_col_deg(H):
+    return int(np.max(sum(h.col_degrees() for h in H)))
+
+
+@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed", "f32-resident", "f16", "bf16"])
 def test_rate07_n65536_subset_bit_exact(mbp, mode):
     """n=65536, R=0.7, d_v {2,3,8}, u=2, QBER 2%: 64 frames, max 60 iterations."""
     w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 64, 0.02)
@@ -399,3 +427,51 @@ def test_resident_barrier_timeout_reports_etimeout(mbp, monkeypatch):
     out = mbp.mbp_decode_bsc(codes, y, e, z, 10, schedule=mbp.SCHED_RESIDENT)
     ref = mbp.mbp_decode_bsc(codes, y, e, z, 10, schedule=mbp.SCHED_STREAMING)
     assert torch.equal(out["x_hat_bits"], ref["x_hat_bits"]) and torch.equal(out["iters"], ref["iters"])
+
+
+@pytest.mark.slow
+def test_precision_sweep_rate07_n65536(mbp):
+    """FP16 and BF16 message storage against FP32 on the n=65536 rate-0.7 code: QBER 1..5%, 2048 frames each.
+
+    Reports FER, mean iterations and (on 4 frames) the largest |L_V - oracle| over iterations 1..5; requires
+    that the half-precision forms fail no more frames than FP32 plus a margin, and that every frame reported
+    as a success satisfies all syndromes.
+    """
+    import json, os
+    H = mi.make_codes(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1)
+    codes = mbp.mbp_create_codes(H)
+    rows = []
+    for q in (0.01, 0.02, 0.03, 0.04, 0.05):
+        x, y, e = mi.bsc_frames(65536, 2048, q, seed=31, stream=int(q * 1000))
+        z = gpu_syndrome(mbp, codes, x)
+        yd, ed = dev(u32_to_i32(y)), dev(e)
+        zz = orc.syndrome(H, x[:4])
+        LP = orc.bsc_llr(y[:4], 65536, e[:4])
+        refs = [orc.decode(H, LP, zz, t, early_exit=False, want_lv=True, threads=4)["L_V"] for t in range(1, 6)]
+        row = {"qber": q}
+        for name, dt in (("f32", mbp.MSG_F32), ("f16", mbp.MSG_F16), ("bf16", mbp.MSG_BF16)):
+            out = mbp.mbp_decode_bsc(codes, yd, ed, z, 60, msg_dtype=dt)
+            xh = host_u32(out["x_hat_bits"])
+            ok = out["success"].cpu().numpy().astype(bool)
+            frame_err = ~ok | ~np.all(xh == x, axis=1)
+            errs = []
+            for t in range(1, 6):
+                o = mbp.mbp_decode_bsc(codes, yd[:4], ed[:4], z_first(mbp, codes, z, 2048, 4), t, msg_dtype=dt,
+                                       early_exit=False, want_soft=True)
+                errs.append(float(np.max(np.abs(o["soft"].cpu().numpy() - refs[t - 1]))))
+            row[name] = {"fer": float(frame_err.mean()), "mean_iters": float(out["iters"].float().mean()),
+                         "max_llr_err_t1_5": errs}
+        rows.append(row)
+        assert row["f16"]["fer"] <= row["f32"]["fer"] + 3 / 2048
+        assert row["bf16"]["fer"] <= row["f32"]["fer"] + 3 / 2048
+        assert row["f32"]["max_llr_err_t1_5"][0] <= 1e-3
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open(os.path.join("gpurun_out", "precision_sweep.json"), "w") as f:
+        json.dump(rows, f, indent=1)
+    print(json.dumps(rows))
+
+
+def z_first(mbp, codes, z_flat, F, k):
+    """The syndromes of the first k frames out of a flat [u][F][W_l] array."""
+    parts = mbp.split_syndromes(codes, z_flat, F)
+    return mbp.join_syndromes([p[:k] for p in parts])
