@@ -8,6 +8,9 @@ The arithmetic lives in ``mbp_oracle.c`` (plain C, double precision), loaded
 with ctypes; this file only marshals arguments. See that file's header for the
 equations it follows and the readings of the paper it takes.
 
+``nbp.py`` (plain PyTorch CPU float64) is the reference of the unrolled,
+normalised BP with learnable scale and offset and of its gradient (autograd).
+
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute-force enumeration, GF(2) elimination and
 invariants; none is "parity unpinned".
