@@ -58,6 +58,10 @@ def _configure(lib):
     lib.orc_check_node_tanh.argtypes = [I, P, I, D, P]
     lib.orc_decode.restype = I
     lib.orc_decode.argtypes = [I, I, P, P, P, I, P, P, I, D, I, I, P, P, P, P, P, P]
+    lib.orc_decode_ex.restype = I
+    lib.orc_decode_ex.argtypes = [I, I, P, P, P, I, P, P, I, D, I, I, I, I, P, P, P, P, P, P]
+    lib.orc_check_node_minsum.restype = I
+    lib.orc_check_node_minsum.argtypes = [I, P, I, D, P]
     return lib
 
 
@@ -153,10 +157,22 @@ def check_node_tanh(v2c, z: int, l_max: float = L_MAX_DEFAULT) -> np.ndarray:
     return out
 
 
+def check_node_minsum(v2c, z: int, l_max: float = L_MAX_DEFAULT) -> np.ndarray:
+    """The min-sum check rule (variant): sign of the others and z, smallest other magnitude."""
+    v = np.ascontiguousarray(v2c, dtype=np.float64)
+    out = np.zeros_like(v)
+    _load().orc_check_node_minsum(len(v), v.ctypes.data, int(z), float(l_max), out.ctypes.data)
+    return out
+
+
+RULES = {"sum-product": 0, "min-sum": 1}
+UPDATES = {"flooding": 0, "matrix-serial": 1}
+
+
 def decode(codes, L_P: np.ndarray, z_bits, max_iter: int, l_max: float = L_MAX_DEFAULT,
            early_exit: bool = True, threads: int = 1, want_lv: bool = False, want_c2v: bool = False,
-           want_synd: bool = False) -> dict:
-    """Algorithm 1 (flooding MBP) on F frames.
+           want_synd: bool = False, rule: str = "sum-product", update: str = "flooding") -> dict:
+    """Algorithm 1 (flooding MBP) on F frames; rule="min-sum" and update="matrix-serial" select the variants.
 
     L_P [F, n] float64; z_bits: list of u arrays [F, ceil(m_l/32)] (or one flat
     array in the [u][F][words] layout). Returns a dict with x_hat_bits, iters,
@@ -180,9 +196,10 @@ def decode(codes, L_P: np.ndarray, z_bits, max_iter: int, l_max: float = L_MAX_D
     lv = np.zeros((F, n), dtype=np.float64) if want_lv else None
     cv = np.zeros((F, e_tot), dtype=np.float64) if want_c2v else None
     ptr = lambda a: a.ctypes.data if a is not None else None
-    rc = _load().orc_decode(len(codes), n, m.ctypes.data, rp.ctypes.data, ci.ctypes.data, F, LP.ctypes.data,
-                            z.ctypes.data, int(max_iter), float(l_max), int(bool(early_exit)), int(threads),
-                            xh.ctypes.data, it.ctypes.data, ok.ctypes.data, ptr(so), ptr(lv), ptr(cv))
+    rc = _load().orc_decode_ex(len(codes), n, m.ctypes.data, rp.ctypes.data, ci.ctypes.data, F, LP.ctypes.data,
+                               z.ctypes.data, int(max_iter), float(l_max), int(bool(early_exit)), RULES[rule],
+                               UPDATES[update], int(threads), xh.ctypes.data, it.ctypes.data, ok.ctypes.data,
+                               ptr(so), ptr(lv), ptr(cv))
     if rc:
         raise RuntimeError(f"orc_decode rc={rc}")
     out = dict(x_hat_bits=xh, iters=it, success=ok)

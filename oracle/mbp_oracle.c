@@ -29,6 +29,9 @@
  *  - A check's extrinsic combination excludes its own edge by prefix/suffix
  *    combination, never by division.
  *  - Hard decision: bit 1 iff L_V < 0 (a tie gives 0).
+ *  - Variants (orc_decode_ex): the min-sum check rule and the matrix-by-matrix
+ *    schedule of Algorithm 1's loop nesting, for comparison with the flooding
+ *    sum-product decoder the paper's text describes.
  *  - The syndrome is tested before the first iteration (iters = 0 on success);
  *    iters counts full check+variable iterations; on failure the result is the
  *    last iteration's hard decision with iters = max_iter.
@@ -235,11 +238,32 @@ int orc_check_node_tanh(int d, const double* v2c, int z, double L_max, double* c
   return 0;
 }
 
+/*
+ * Min-sum check-node rule (an algorithm variant, not in the paper): the
+ * magnitude of the extrinsic combination is replaced by the smallest magnitude
+ * among the other incoming messages, the sign kept:
+ * c2v[k] = (-1)^z prod_{r != k} sgn(v2c[r]) * min_{r != k} |v2c[r]|, clipped.
+ */
+int orc_check_node_minsum(int d, const double* v2c, int z, double L_max, double* c2v) {
+  for (int k = 0; k < d; ++k) {
+    double s = z ? -1.0 : 1.0, mn = INFINITY;
+    for (int r = 0; r < d; ++r) {
+      if (r == k) continue;
+      s *= sgn(v2c[r]);
+      if (fabs(v2c[r]) < mn) mn = fabs(v2c[r]);
+    }
+    c2v[k] = clip(s * mn, L_max);
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------ Algorithm 1 */
 
 typedef struct {
   const orc_code* C;
   int F, T, early_exit;
+  int rule;                 /* 0: sum-product (eq. 6), 1: min-sum */
+  int serial;               /* 0: flooding over all matrices, 1: matrix by matrix (Algorithm 1's nesting) */
   double L_max;
   const double* L_P;        /* [F][n] */
   const uint32_t* z_bits;   /* [u][F][words(m_l)] */
@@ -283,29 +307,37 @@ static int decode_one(const job_t* J, int f, double* c2v, double* v2c, double* L
   } else {
     for (int64_t e = 0; e < C->e_tot; ++e) c2v[e] = 0.0; /* Algorithm 1: V2C starts at L_P */
     for (t = 1; t <= J->T; ++t) {
-      /* variable-to-check: L_P plus every other incoming check message, all matrices */
-      for (int i = 0; i < n; ++i) {
-        for (int64_t a = C->col_ptr[i]; a < C->col_ptr[i + 1]; ++a) {
-          double s = LP[i];
-          for (int64_t b = C->col_ptr[i]; b < C->col_ptr[i + 1]; ++b)
-            if (b != a) s += c2v[C->col_edge[b]];
-          v2c[C->col_edge[a]] = clip(s, L);
+      /* flooding: one step over every check of every matrix; matrix-serial: one step per matrix, each
+         using the posterior that the previous matrix's step left */
+      const int steps = J->serial ? C->u : 1;
+      for (int step = 0; step < steps; ++step) {
+        const int32_t r0 = J->serial ? C->row_first[step] : 0;
+        const int32_t r1 = J->serial ? C->row_first[step + 1] : C->m_tot;
+        /* variable-to-check: L_P plus every other incoming check message, all matrices */
+        for (int32_t r = r0; r < r1; ++r)
+          for (int64_t a = C->row_ptr[r]; a < C->row_ptr[r + 1]; ++a) {
+            const int i = C->edge_col[a];
+            double s = LP[i];
+            for (int64_t b = C->col_ptr[i]; b < C->col_ptr[i + 1]; ++b)
+              if (C->col_edge[b] != a) s += c2v[C->col_edge[b]];
+            v2c[a] = clip(s, L);
+          }
+        /* check-to-variable, eq. (6) (or the min-sum rule), for every check of the step */
+        for (int32_t r = r0; r < r1; ++r) {
+          int l = C->row_mat[r];
+          int zj = bit_of(J->z_bits + z_offset(C, J->F, l, f), C->row_local[r]);
+          int d = (int)(C->row_ptr[r + 1] - C->row_ptr[r]);
+          for (int k = 0; k < d; ++k) vin[k] = v2c[C->row_ptr[r] + k];
+          if (J->rule == 1) orc_check_node_minsum(d, vin, zj, L, vout);
+          else if (orc_check_node(d, vin, zj, L, vout)) return -2;
+          for (int k = 0; k < d; ++k) c2v[C->row_ptr[r] + k] = vout[k];
         }
-      }
-      /* check-to-variable, eq. (6), for every check of every matrix */
-      for (int32_t r = 0; r < C->m_tot; ++r) {
-        int l = C->row_mat[r];
-        int zj = bit_of(J->z_bits + z_offset(C, J->F, l, f), C->row_local[r]);
-        int d = (int)(C->row_ptr[r + 1] - C->row_ptr[r]);
-        for (int k = 0; k < d; ++k) vin[k] = v2c[C->row_ptr[r] + k];
-        if (orc_check_node(d, vin, zj, L, vout)) return -2;
-        for (int k = 0; k < d; ++k) c2v[C->row_ptr[r] + k] = vout[k];
-      }
-      /* soft decision, eq. (2): L_V = L_P + sum over l and checks of C2V, in (l, j) order */
-      for (int i = 0; i < n; ++i) {
-        double s = LP[i];
-        for (int64_t a = C->col_ptr[i]; a < C->col_ptr[i + 1]; ++a) s += c2v[C->col_edge[a]];
-        LV[i] = s;
+        /* soft decision, eq. (2): L_V = L_P + sum over l and checks of C2V, in (l, j) order */
+        for (int i = 0; i < n; ++i) {
+          double s = LP[i];
+          for (int64_t a = C->col_ptr[i]; a < C->col_ptr[i + 1]; ++a) s += c2v[C->col_edge[a]];
+          LV[i] = s;
+        }
       }
       /* hard decision */
       for (int i = 0; i < n; ++i) set_bit(xhat, i, LV[i] < 0.0);
@@ -355,13 +387,18 @@ static void* run_job(void* arg) {
  * test as success. Optional outputs (NULL to skip): synd_ok [F][u], L_V_out
  * [F][n], c2v_out [F][e_tot] in stacked CSR edge order (matrix 1's edges, then
  * matrix 2's, ...). Frames are spread over n_threads POSIX threads.
+ * rule: 0 = sum-product (eq. 6), 1 = min-sum. serial: 0 = flooding over every
+ * matrix; 1 = matrix by matrix, the literal nesting of Algorithm 1 (for each H_l
+ * in turn the V2C of its edges, its checks and the soft decision of eq. 2;
+ * the stopping rule after all u). Both are variants; the paper's decoder is
+ * rule 0 with flooding.
  * Returns 0, -1 (bad arguments) or -2 (out of memory).
  */
-int orc_decode(int u, int n, const int32_t* m, const int32_t* row_ptr_cat, const int32_t* col_idx_cat,
-               int F, const double* L_P, const uint32_t* z_bits, int max_iter, double L_max,
-               int early_exit, int n_threads, uint32_t* x_hat_bits, int32_t* iters, uint8_t* success,
-               uint8_t* synd_ok, double* L_V_out, double* c2v_out) {
-  if (F < 0 || max_iter < 0 || !(L_max > 0)) return -1;
+int orc_decode_ex(int u, int n, const int32_t* m, const int32_t* row_ptr_cat, const int32_t* col_idx_cat,
+                  int F, const double* L_P, const uint32_t* z_bits, int max_iter, double L_max,
+                  int early_exit, int rule, int serial, int n_threads, uint32_t* x_hat_bits, int32_t* iters,
+                  uint8_t* success, uint8_t* synd_ok, double* L_V_out, double* c2v_out) {
+  if (F < 0 || max_iter < 0 || !(L_max > 0) || rule < 0 || rule > 1 || serial < 0 || serial > 1) return -1;
   orc_code C;
   int rc = code_build(&C, u, n, m, row_ptr_cat, col_idx_cat);
   if (rc) { code_free(&C); return rc; }
@@ -373,6 +410,7 @@ int orc_decode(int u, int n, const int32_t* m, const int32_t* row_ptr_cat, const
   for (int k = 0; k < n_threads; ++k) {
     job_t* J = &jobs[k];
     J->C = &C; J->F = F; J->T = max_iter; J->early_exit = early_exit; J->L_max = L_max;
+    J->rule = rule; J->serial = serial;
     J->L_P = L_P; J->z_bits = z_bits; J->x_hat_bits = x_hat_bits; J->iters = iters; J->success = success;
     J->synd_ok = synd_ok; J->L_V_out = L_V_out; J->c2v_out = c2v_out;
     J->f_begin = (int)((int64_t)F * k / n_threads);
@@ -388,4 +426,13 @@ int orc_decode(int u, int n, const int32_t* m, const int32_t* row_ptr_cat, const
   free(th);
   code_free(&C);
   return rc;
+}
+
+/* Algorithm 1 as above: flooding, sum-product (eq. 6). */
+int orc_decode(int u, int n, const int32_t* m, const int32_t* row_ptr_cat, const int32_t* col_idx_cat,
+               int F, const double* L_P, const uint32_t* z_bits, int max_iter, double L_max,
+               int early_exit, int n_threads, uint32_t* x_hat_bits, int32_t* iters, uint8_t* success,
+               uint8_t* synd_ok, double* L_V_out, double* c2v_out) {
+  return orc_decode_ex(u, n, m, row_ptr_cat, col_idx_cat, F, L_P, z_bits, max_iter, L_max, early_exit, 0, 0,
+                       n_threads, x_hat_bits, iters, success, synd_ok, L_V_out, c2v_out);
 }

@@ -40,11 +40,21 @@ def _llr_pin():
         pins.test_bsc_llr_is_channel_likelihood_ratio(e)
 
 
+def _minsum_pin():
+    import test_oracle_variants as var
+    for u in (1, 2):
+        for trial in range(3):
+            var.test_minsum_tree_codes_reach_max_log_posteriors(u, trial)
+    for d in (3, 4):
+        var.test_minsum_bracketed_by_sum_product(d)
+
+
 MUTATIONS = {
     # variable-to-check message forgets the channel prior
-    "v2c_drops_prior": ("          double s = LP[i];\n          for (int64_t b", "          double s = 0.0;\n          for (int64_t b", _tree_pin),
+    "v2c_drops_prior": ("            double s = LP[i];\n            for (int64_t b",
+                        "            double s = 0.0;\n            for (int64_t b", _tree_pin),
     # variable-to-check message keeps its own check's message (not extrinsic)
-    "v2c_not_extrinsic": ("if (b != a) s += c2v[C->col_edge[b]];", "s += c2v[C->col_edge[b]];", _tree_pin),
+    "v2c_not_extrinsic": ("if (C->col_edge[b] != a) s += c2v[C->col_edge[b]];", "s += c2v[C->col_edge[b]];", _tree_pin),
     # syndrome sign of eq. (6) ignored
     "c2v_ignores_syndrome": ("double s = z ? -1.0 : 1.0;\n  for (int k = 0; k < d; ++k) {\n    double ext;",
                              "double s = 1.0;\n  for (int k = 0; k < d; ++k) {\n    double ext;", _tree_pin),
@@ -53,11 +63,18 @@ MUTATIONS = {
     # prefix combination shifted by one edge
     "prefix_off_by_one": ("orc_boxplus(pre[k - 1], v2c[k - 1])", "orc_boxplus(pre[k - 1], v2c[k])", _parity_pin),
     # posterior of eq. (2) forgets the channel prior
-    "posterior_drops_prior": ("        double s = LP[i];\n        for (int64_t a", "        double s = 0.0;\n        for (int64_t a", _tree_pin),
+    "posterior_drops_prior": ("          double s = LP[i];\n          for (int64_t a",
+                              "          double s = 0.0;\n          for (int64_t a", _tree_pin),
     # hard decision with the wrong orientation
     "hard_decision_flipped": ("set_bit(xhat, i, LV[i] < 0.0);", "set_bit(xhat, i, LV[i] > 0.0);", _frames_pin),
     # syndrome of eq. (1) reads the wrong bit of x
     "syndrome_wrong_bit": ("p ^= bit_of(x, C->edge_col[k]);", "p ^= bit_of(x, C->edge_col[k] + 1);", _syndrome_pin),
+    # min-sum rule takes its own edge into the minimum (not extrinsic)
+    "minsum_not_extrinsic": ("      if (r == k) continue;\n      s *= sgn(v2c[r]);", "      s *= sgn(v2c[r]);",
+                             _minsum_pin),
+    # min-sum rule ignores the syndrome bit
+    "minsum_ignores_syndrome": ("    double s = z ? -1.0 : 1.0, mn = INFINITY;", "    double s = 1.0, mn = INFINITY;",
+                                _minsum_pin),
     # eq. (5) with P^0 and P^1 swapped
     "llr_orientation": ("L_P[i] = log(p0 / p1);", "L_P[i] = log(p1 / p0);", _llr_pin),
 }
