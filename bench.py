@@ -56,8 +56,16 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--accumulate", default="auto", choices=["auto", "float", "fixed"],
                    help="eq. (2) accumulation: fixed-point single pass or float second pass")
-    p.add_argument("--schedule", default="auto", choices=["auto", "streaming", "resident"],
-                   help="kernels per iteration, or one cooperative launch keeping tile groups in L2")
+    p.add_argument("--schedule", default="auto", choices=["auto", "streaming", "resident", "graph"],
+                   help="kernels per iteration, one cooperative launch keeping tile groups in L2, or persistent "
+                        "kernels with the iteration loop in a CUDA graph")
+    p.add_argument("--rule", default="sum-product", choices=["sum-product", "min-sum"],
+                   help="check-node rule: eq. (6) or the min-sum approximation (variant)")
+    p.add_argument("--update", default="flooding", choices=["flooding", "matrix-serial"],
+                   help="update order: flooding over all matrices, or matrix by matrix (variant)")
+    p.add_argument("--workload", default="n65536", choices=["n65536", "uneven"],
+                   help="n65536: the rate-0.7 n=65536 batch; uneven: 4096 frames of 24 codes "
+                        "(n 2^14..2^18, R 0.5..0.8, u 2..3, QBER U[1%%, 4%%]) in one grouped call")
     p.add_argument("--msg-dtype", default="f32", choices=["f32", "f16", "bf16"],
                    help="message storage: FP32, or FP16/BF16 with FP32 arithmetic")
     return p.parse_args()
@@ -174,17 +182,30 @@ def oracle_time(H, x, y, e, frames, threads):
     return dt, out
 
 
-def kernel_traffic(iters, launches, summary):
+KERNEL_SOURCES = ("mbp_internal.h", "mbp_device.cuh", "mbp_stream.cuh", "mbp_stream_f32.cu", "mbp_resident.cuh")
+
+
+def kernel_source_digest():
+    """First 16 hex digits of the SHA-256 of the sources that define the decoder kernels (the key a committed
+    ncu summary records, so that its DRAM figures are used only for the kernels they were measured on)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2001_07979_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(iters, launches, summary, msg_dtype):
     """Mean DRAM bytes per launch of the dominant kernel, from the committed full-size ncu capture (bytes per
-    frame in a frame's first iteration and in a later one), if that capture was taken on the current source."""
+    frame in a frame's first iteration and in a later one), if that capture was taken on the current source
+    with the same message type."""
     path = os.path.join(ROOT, "profiles", summary)
-    src = os.path.join(ROOT, "paper_2001_07979_gb300", "csrc", "mbp_kernels.cu")
     try:
         text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         kv = dict(line.split("=", 1) for line in text.splitlines() if "=" in line and not line.startswith("#"))
         kv = {k.strip(): v.strip() for k, v in kv.items()}
-        if kv.get("kernel_source_sha256_16") != digest or not launches:
+        if kv.get("kernel_source_sha256_16") != kernel_source_digest() or not launches:
+            return None
+        if kv.get("msg_dtype", "f32") != msg_dtype:
             return None
         it = np.asarray(iters, dtype=np.int64)
         first, later = int(np.sum(it >= 1)), int(np.sum(np.maximum(it - 1, 0)))
@@ -254,15 +275,18 @@ def run_gb300(args):
     zd = mbp.mbp_syndrome(codes, xd)  # Alice's side, untimed
     msg = {"f32": mbp.MSG_F32, "f16": mbp.MSG_F16, "bf16": mbp.MSG_BF16}[args.msg_dtype]
     msg_bytes = {"f32": 4, "f16": 2, "bf16": 2}[args.msg_dtype]
-    ws = torch.empty(mbp.mbp_decode_workspace_size(codes, F, msg), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     acc = {"auto": mbp.ACC_AUTO, "float": mbp.ACC_FLOAT, "fixed": mbp.ACC_FIXED}[args.accumulate]
-    sched = {"auto": mbp.SCHED_AUTO, "streaming": mbp.SCHED_STREAMING, "resident": mbp.SCHED_RESIDENT}[args.schedule]
+    sched = {"auto": mbp.SCHED_AUTO, "streaming": mbp.SCHED_STREAMING, "resident": mbp.SCHED_RESIDENT,
+             "graph": mbp.SCHED_GRAPH}[args.schedule]
+    ws = torch.empty(mbp.mbp_decode_workspace_size(codes, F, msg, schedule=sched), dtype=torch.uint8, device=dev)
+    variant = dict(rule=mbp.RULE_MIN_SUM if args.rule == "min-sum" else mbp.RULE_SUM_PRODUCT,
+                   update=mbp.UPDATE_MATRIX_SERIAL if args.update == "matrix-serial" else mbp.UPDATE_FLOODING)
 
     def step():
         return mbp.mbp_decode_bsc(codes, yd, ed, zd, MAX_ITER, msg_dtype=msg, l_max=L_MAX, workspace=ws,
-                                  accumulate=acc, schedule=sched)
+                                  accumulate=acc, schedule=sched, **variant)
 
     for _ in range(max(args.warmup, 3)):
         out = step()
@@ -275,18 +299,23 @@ def run_gb300(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    mbp.mbp_profile_enable(True)
     ev0.record(stream)
     for _ in range(args.steps):
         out = step()
     ev1.record(stream)
     torch.cuda.synchronize()
-    prof = mbp.mbp_profile_get()
-    mbp.mbp_profile_enable(False)
     if world > 1:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     clk = clocks.stop()
+    # per-kernel device times: the same steps again with a CUDA event pair around every kernel launch on the
+    # decode stream (the graph schedule's kernels are then launched from the host, one per event pair)
+    mbp.mbp_profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = mbp.mbp_profile_get()
+    mbp.mbp_profile_enable(False)
 
     iters = out["iters"].cpu().numpy()
     ok = out["success"].cpu().numpy().astype(bool)
@@ -302,11 +331,12 @@ def run_gb300(args):
     outh = dict(x_hat_bits=torch.empty((F, Wn), dtype=torch.int32).pin_memory(),
                 iters=torch.empty(F, dtype=torch.int32).pin_memory(),
                 success=torch.empty(F, dtype=torch.uint8).pin_memory())
-    wsh = torch.empty(mbp.mbp_decode_workspace_size(codes, F, msg, host_io=True), dtype=torch.uint8, device=dev)
+    wsh = torch.empty(mbp.mbp_decode_workspace_size(codes, F, msg, host_io=True, schedule=sched), dtype=torch.uint8,
+                      device=dev)
 
     def step_e2e():
         mbp.mbp_decode_bsc_host(codes, yh, eh, zh, MAX_ITER, msg_dtype=msg, l_max=L_MAX, workspace=wsh, out=outh,
-                                accumulate=acc, schedule=sched)
+                                accumulate=acc, schedule=sched, **variant)
 
     for _ in range(2):
         step_e2e()
@@ -341,12 +371,12 @@ def run_gb300(args):
         n_dom, ms_dom = prof["persistent"]
         kernel_name = "resident_kernel (all steps of eq. 6, eq. 2 and the stopping rule, tile groups in L2)"
         b_dom, rule = b_path, "2*s*E+12n per frame-iteration (s*E less in a frame's first)"
-        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "resident_kernel_n65536.txt")
+        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "resident_kernel_n65536.txt", args.msg_dtype)
     else:
         n_dom, ms_dom = prof["check"]
         kernel_name = "cn_kernel (check-node update, eq. 6)"
         b_dom, rule = b_check, "per frame: s*E+4n per iteration, plus s*E per iteration after the first"
-        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "check_node_kernel_n65536.txt")
+        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "check_node_kernel_n65536.txt", args.msg_dtype)
     achieved = b_dom * args.steps / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
 
     result = None
@@ -361,7 +391,8 @@ def run_gb300(args):
                        "mean_iterations": float(iters.mean()), "max_iterations": int(iters.max()),
                        "fer": fails / (F * world), "undetected_errors": undetected,
                        "l2": "per-step decoder state ~2.8 GB > 129 MB L2 (no flush)",
-                       "accumulate": args.accumulate, "schedule": args.schedule,
+                       "accumulate": args.accumulate, "schedule": args.schedule, "rule": args.rule,
+                       "update": args.update,
                        "parallelism": f"replicas x{world} (frames sharded, no collective on the path)"},
             "roofline": {"bound": "hbm", "kernel": kernel_name,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -374,6 +405,7 @@ def run_gb300(args):
                          "path_gbs": path_gbs, "path_frac": path_gbs / peak,
                          "path_bytes_rule": "2*s*E+12n per frame-iteration (s*E less in a frame's first)"},
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()},
+            "kernel_ms_source": "a second pass of the same steps with a CUDA event pair around every kernel launch",
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": {"value": value_e2e, "unit": "Mbps", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -396,10 +428,100 @@ def run_gb300(args):
     return 0
 
 
+UNEVEN_FRAMES, UNEVEN_SEED = 4096, 4
+UNEVEN_WORKLOAD = ("MBP grouped decode of uneven frames: 4096 frames, each of a code drawn from n in {2^14, 2^16, "
+                   "2^18} x R in {0.5, 0.6, 0.7, 0.8} x u in {2, 3} (24 PEG codes, dv {2:.3,3:.4,8:.3}), QBER "
+                   "uniform in [1%, 4%] per frame, max 60 it")
+
+
+def run_uneven(args):
+    """One step = one mbp_decode_multi call over the whole uneven batch (launch shapes from the autotuner,
+    untimed); beside it, the same frames decoded by one single-code streaming call per code."""
+    import torch
+
+    import paper_2001_07979_gb300 as mbp
+
+    torch.cuda.set_device(0)
+    mbp.build()
+    mbp._load()
+    dev = torch.device("cuda", 0)
+    frames = UNEVEN_FRAMES if args.frames == FRAMES else args.frames
+    specs = mi.uneven_batch(frames, UNEVEN_SEED)
+    msg = {"f32": mbp.MSG_F32, "f16": mbp.MSG_F16, "bf16": mbp.MSG_BF16}[args.msg_dtype]
+    groups, xs, bits = [], [], 0
+    for sp in specs:
+        H = mi.make_codes(sp["n"], sp["m"], sp["dist"], sp["u"], sp["cfg_seed"])
+        x, y, e = mi.bsc_frames(sp["n"], sp["frames"], sp["qber"], seed=sp["cfg_seed"])
+        codes = mbp.mbp_create_codes(H)
+        xd = torch.from_numpy(x.view(np.int32)).to(dev)
+        groups.append(dict(codes=codes, y_bits=torch.from_numpy(y.view(np.int32)).to(dev),
+                           qber=torch.from_numpy(e).to(dev), z_bits=mbp.mbp_syndrome(codes, xd)))
+        xs.append(x)
+        bits += sp["n"] * sp["frames"]
+    ws = torch.empty(mbp.mbp_multi_workspace_size(groups, msg), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    _, tuning = mbp.mbp_autotune_multi(groups, MAX_ITER, msg_dtype=msg, l_max=L_MAX, workspace=ws)
+
+    def step():
+        return mbp.mbp_decode_multi(groups, MAX_ITER, msg_dtype=msg, l_max=L_MAX, workspace=ws)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            r = fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps, r
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms, outs = timed(step)
+    clk = clocks.stop()
+    # the same frames, one single-code call (streaming schedule) per code
+    wss = [torch.empty(mbp.mbp_decode_workspace_size(g["codes"], g["y_bits"].shape[0], msg), dtype=torch.uint8,
+                       device=dev) for g in groups]
+
+    def step_single():
+        return [mbp.mbp_decode_bsc(g["codes"], g["y_bits"], g["qber"], g["z_bits"], MAX_ITER, msg_dtype=msg,
+                                   l_max=L_MAX, workspace=w, schedule=mbp.SCHED_STREAMING)
+                for g, w in zip(groups, wss)]
+
+    ms_single, outs_single = timed(step_single)
+    same = all(torch.equal(a[k], b[k]) for a, b in zip(outs, outs_single) for k in ("x_hat_bits", "iters", "success"))
+    fails = undetected = 0
+    it_sum = 0
+    for o, x in zip(outs, xs):
+        ok = o["success"].cpu().numpy().astype(bool)
+        xh = o["x_hat_bits"].cpu().numpy().view(np.uint32)
+        fails += int((~ok).sum())
+        undetected += int(np.sum(ok & ~np.all(xh == x, axis=1)))
+        it_sum += int(o["iters"].sum().item())
+    line = {
+        "metric": METRIC, "value": bits / (ms / 1e3) / 1e6, "unit": "Mbps", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.msg_dtype if args.msg_dtype == "f32" else f"{args.msg_dtype}+f32", "data": "synthetic",
+        "config": {"workload": UNEVEN_WORKLOAD, "frames": frames, "codes": len(groups), "bits_per_step": bits,
+                   "fer": fails / frames, "undetected_errors": undetected, "mean_iterations": it_sum / frames,
+                   "tuning": tuning, "l2": "per-step decoder state of several GB > 129 MB L2 (no flush)"},
+        "single_code_calls": {"ms_per_step": ms_single, "value": bits / (ms_single / 1e3) / 1e6,
+                              "outputs_identical": same},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
     return run_gb300(args)
 
 

@@ -81,18 +81,48 @@ enum { MBP_ACC_AUTO = 0, MBP_ACC_FLOAT = 1, MBP_ACC_FIXED = 2 };
  * How the iterations are scheduled on the GPU (results are the same):
  *  MBP_SCHED_STREAMING  one kernel per step (check nodes, variable nodes,
  *                       syndrome test, retirement) per iteration over every
- *                       tile of 8 frames that is still decoding; messages
- *                       stream through HBM each iteration;
+ *                       tile of 32 frames that is still decoding; messages
+ *                       stream through HBM each iteration, and the host reads
+ *                       the number of unfinished tiles after each iteration;
  *  MBP_SCHED_RESIDENT   one cooperative launch that takes the tiles a group at
  *                       a time, as many as keep the group's messages within
  *                       3/4 of L2, and runs all of a group's iterations with
  *                       grid-wide barriers between the steps; needs floating-
- *                       point accumulation. A barrier that waits longer than
- *                       about 2 s ends the decode with MBP_ETIMEOUT;
+ *                       point accumulation and FP32 or FP64 storage. A barrier
+ *                       that waits longer than about 2 s ends the decode with
+ *                       MBP_ETIMEOUT;
+ *  MBP_SCHED_GRAPH      the schedule of mbp_decode_multi with one group:
+ *                       persistent kernels over a device-built list of the
+ *                       unfinished tiles, the iteration loop inside a CUDA
+ *                       graph (a WHILE node that the retirement kernel drives),
+ *                       so no host round trip per iteration; FP32, FP16 or
+ *                       BF16 storage, floating-point accumulation. The
+ *                       workspace layout differs (size it with this schedule);
  *  MBP_SCHED_AUTO       (default) STREAMING, which measures faster on GB300
  *                       for the benchmark workload.
  */
-enum { MBP_SCHED_AUTO = 0, MBP_SCHED_STREAMING = 1, MBP_SCHED_RESIDENT = 2 };
+enum { MBP_SCHED_AUTO = 0, MBP_SCHED_STREAMING = 1, MBP_SCHED_RESIDENT = 2, MBP_SCHED_GRAPH = 3 };
+
+/*
+ * Algorithm variants (they change the results; the defaults are the paper's
+ * decoder). Check-node rule:
+ *  MBP_RULE_SUM_PRODUCT  eq. (6), the exact sum-product combination (default);
+ *  MBP_RULE_MIN_SUM      the min-sum approximation: sign as eq. (6), magnitude
+ *                        the smallest magnitude among the other incoming
+ *                        messages (float arithmetic: FP32, FP16 or BF16 storage).
+ * Update order:
+ *  MBP_UPDATE_FLOODING      every check of every matrix reads the previous
+ *                           iteration's messages (default);
+ *  MBP_UPDATE_MATRIX_SERIAL Algorithm 1's loop nesting taken literally: within
+ *                           an iteration, H_1's checks then the soft decision of
+ *                           eq. (2), then H_2's checks (reading that posterior)
+ *                           and eq. (2), and so on; the stopping rule after all
+ *                           u matrices.
+ * Both variants run with the streaming schedule (AUTO or STREAMING) and
+ * floating-point accumulation.
+ */
+enum { MBP_RULE_SUM_PRODUCT = 0, MBP_RULE_MIN_SUM = 1 };
+enum { MBP_UPDATE_FLOODING = 0, MBP_UPDATE_MATRIX_SERIAL = 1 };
 
 /* One binary m x n matrix in compressed sparse rows, host memory, 0-based. */
 typedef struct {
@@ -120,7 +150,9 @@ typedef struct {
                              each frame ran (double for F64, float for the others); NULL to skip */
   uint8_t* synd_ok;       /* optional device [F][u]: 1 where H_l x_hat = z^l for the output bits */
   int32_t accumulate;     /* MBP_ACC_AUTO (default), MBP_ACC_FLOAT or MBP_ACC_FIXED */
-  int32_t schedule;       /* MBP_SCHED_AUTO (default), MBP_SCHED_STREAMING or MBP_SCHED_RESIDENT */
+  int32_t schedule;       /* MBP_SCHED_AUTO (default), MBP_SCHED_STREAMING, MBP_SCHED_RESIDENT or MBP_SCHED_GRAPH */
+  int32_t rule;           /* MBP_RULE_SUM_PRODUCT (default) or MBP_RULE_MIN_SUM */
+  int32_t update;         /* MBP_UPDATE_FLOODING (default) or MBP_UPDATE_MATRIX_SERIAL */
 } mbp_opts;
 
 /* Fill *opts with the defaults above (F32, early exit, l_max 20, no workspace). */
@@ -219,6 +251,114 @@ int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int fram
                    mbp_stream_t stream);
 
 /*
+ * Grouped decode of uneven frames. The paper splits a sifted key into k frames
+ * of n bits that are decoded independently with one code (Section 3A); this
+ * entry point decodes frames of several codes in one call: G groups; group g holds F_g
+ * frames of its own code (n, rate, u and the QBER of each frame may all
+ * differ between groups) with the same per-frame semantics as
+ * mbp_decode_batch / mbp_decode_bsc. Every iteration runs one persistent
+ * check-node kernel per check-degree class (at most 8 classes per batch), one
+ * variable-node kernel and one syndrome kernel per class over the frames of
+ * all groups that are still decoding, or (grid kernels, the default unless
+ * mbp_autotune_multi finds the persistent ones faster) every group's
+ * streaming-schedule kernels; a single-block kernel retires finished frames
+ * and rebuilds the work lists on the device. The loop is one CUDA graph
+ * with a WHILE node (built on first use for each workspace, batch shape and
+ * launch shape, then cached by the library), so the call is asynchronous on
+ * `stream`: it returns once the work is queued. opts->validate = 1 adds one host
+ * synchronisation per group (the non-finite check), and while kernel
+ * accounting (mbp_profile_enable) is on the loop is driven from the host with
+ * one read-back per iteration.
+ *
+ * opts: msg_dtype F32 (default), F16 or BF16 (F64 gives MBP_EUNSUPPORTED);
+ * accumulate AUTO or FLOAT; early_exit, l_max and validate as for
+ * mbp_decode_batch; schedule, soft_out, synd_ok and host_io are ignored (the
+ * per-group fields below replace them). workspace: device, 256-byte aligned,
+ * >= mbp_multi_workspace_size() bytes for the same groups and opts.
+ * At most 65535 tiles of 32 frames in all, and at most 256 groups.
+ */
+typedef struct {
+  const mbp_codes* codes;  /* the group's code */
+  int32_t F;               /* frames in the group (>= 0) */
+  const void* llr;         /* device [F][n] float LLRs, or NULL to form eq. (5) from y_bits and qber */
+  const uint32_t* y_bits;  /* device [F][ceil(n/32)] Bob's bits (used when llr is NULL) */
+  const double* qber;      /* device [F] per-frame QBER in (0, 0.5] (used when llr is NULL) */
+  const uint32_t* z_bits;  /* device [u][F][ceil(m_l/32)] Alice's syndromes */
+  uint32_t* x_hat_bits;    /* device [F][ceil(n/32)], written */
+  int32_t* iters;          /* device [F], written */
+  uint8_t* success;        /* device [F], written */
+  uint8_t* synd_ok;        /* optional device [F][u], written */
+  void* soft_out;          /* optional device [F][n] float posterior L_V, written */
+} mbp_group;
+
+int mbp_multi_workspace_size(const mbp_group* groups, int G, const mbp_opts* opts, size_t* bytes);
+int mbp_decode_multi(const mbp_group* groups, int G, int max_iter, const mbp_opts* opts, mbp_stream_t stream);
+
+/*
+ * Launch shapes of the grouped decode and the autotuner that picks them. The
+ * paper chooses its thread-block split by measuring several for its frame
+ * length (Section 3B, Table 1); mbp_autotune_multi makes that search on the
+ * batch at hand: it decodes the batch with each
+ * candidate (first the grid kernels against the persistent kernels; for the
+ * persistent kernels then check-node blocks of 2, 4 or 8 warps on all or half
+ * of the resident block slots, and variable-node and syndrome blocks of 2, 4
+ * or 8 warps; a coordinate search), timing each with CUDA events on `stream`, and
+ * keeps the fastest for later mbp_decode_multi calls with the same codes and
+ * frame counts on this device and message type. The results of every shape
+ * are identical; the outputs are left as a decode with the chosen shape
+ * writes them. Blocks until done. best may be NULL.
+ */
+typedef struct {
+  int32_t grid_kernels; /* 1: every group runs the streaming schedule's kernels (a block per 8 rows or nodes of
+                           every tile); 0: persistent kernels over the device-built lists of unfinished tiles */
+  int32_t cn_warps;   /* warps per block of the check-node kernels */
+  int32_t cn_waves;   /* 1: every resident block slot of the SMs; 2: half of them */
+  int32_t vn_warps;   /* warps per block of the variable-node kernel */
+  int32_t syn_warps;  /* warps per block of the syndrome kernels */
+  double ms;          /* measured time of one decode with this shape */
+} mbp_tuning;
+
+int mbp_autotune_multi(const mbp_group* groups, int G, int max_iter, const mbp_opts* opts, mbp_tuning* best,
+                       mbp_stream_t stream);
+
+/* Drop the library's cached graphs and tuned shapes (for example before freeing a workspace that a cached graph
+ * refers to and allocating another at the same address; a graph never reads a workspace outside a decode call). */
+int mbp_release_cached(void);
+
+/*
+ * Unrolled normalised BP with learnable scalars. The paper's decoder has no
+ * learned parameters; this form unrolls T flooding iterations of the decoder
+ * above (Algorithm 1 with eq. 6 and eq. 2, no early exit) and rescales every
+ * check-to-variable message of matrix l at iteration t as
+ *   C = alpha[t][l] * sgn(c) * max(|c| - beta[t][l], 0),
+ * c being the message of eq. (6) clipped to l_max. alpha = 1, beta = 0 gives
+ * the plain decoder's posteriors bit for bit. FP32 arithmetic; at most 32
+ * edges per check.
+ *
+ * mbp_nbp_forward: llr device [F][n] float channel LLRs; z_bits device
+ * [u][F][ceil(m_l/32)]; alpha, beta device [T][u] float (row t-1 for iteration
+ * t; beta in LLR units); lv_out optional device [T][F][n] float, written: the
+ * posterior L^t of eq. (2) after each iteration. The workspace (device,
+ * 256-byte aligned, >= mbp_nbp_workspace_size bytes) keeps every iteration's
+ * messages and posteriors (the checkpoints of the backward pass).
+ *
+ * mbp_nbp_backward: the gradient of J = sum_t sum_{f,i} grad_lv[t][f][i] L^t[f][i]
+ * (grad_lv device [T][F][n]) with respect to alpha and beta (device [T][u]
+ * float, written) and, if grad_llr is not NULL, the channel LLRs (device
+ * [F][n] float, written). A hand-written adjoint that runs the iterations in
+ * reverse from the checkpoints; it must follow mbp_nbp_forward with the same
+ * codes, F, T, alpha, beta, l_max and workspace. Deterministic (no atomics).
+ * Both calls are asynchronous on `stream`.
+ */
+int mbp_nbp_workspace_size(const mbp_codes* codes, int F, int T, size_t* bytes);
+int mbp_nbp_forward(const mbp_codes* codes, int F, int T, const float* llr, const uint32_t* z_bits,
+                    const float* alpha, const float* beta, double l_max, void* workspace, size_t workspace_bytes,
+                    float* lv_out, mbp_stream_t stream);
+int mbp_nbp_backward(const mbp_codes* codes, int F, int T, const float* alpha, const float* beta, double l_max,
+                     const float* grad_lv, void* workspace, size_t workspace_bytes, float* grad_alpha,
+                     float* grad_beta, float* grad_llr, mbp_stream_t stream);
+
+/*
  * Allocation-free decode. The paper has no counterpart: this entry point
  * exists for callers that can pass device inputs and outputs but cannot call
  * cudaMalloc for a workspace, for example because another runtime owns the
@@ -228,7 +368,8 @@ int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int fram
  * It behaves like mbp_decode_bsc, but keeps the decoder state in a fixed
  * device array of MBP_STATIC_SCRATCH_BYTES inside this library instead of
  * opts->workspace. opts->workspace and opts->workspace_bytes are ignored, and
- * opts->host_io must be 0. The call allocates nothing: no cudaMalloc, no
+ * opts->host_io must be 0; opts->schedule MBP_SCHED_GRAPH gives MBP_EUNSUPPORTED
+ * (instantiating a graph may allocate). The call allocates nothing: no cudaMalloc, no
  * cudaFree, no allocating library routine.
  *  - The array is created when the library's device code is loaded on a GPU.
  *    Every GPU that loads the library holds it until the process exits.

@@ -180,3 +180,28 @@ def bsc_frames(n: int, frames: int, qber, seed: int, stream: int = 0):
 # Workloads of the benchmark and the parity tests, named by what they are.
 CODE_N1024_RATE05_DV3 = dict(n=1024, m=512, dist={3: 1.0}, u=2, seed=0)
 CODE_N65536_RATE07_DV238 = dict(n=65536, m=19661, dist={2: 0.3, 3: 0.4, 8: 0.3}, u=2, seed=1)
+
+
+# Uneven batches: frames of several codes in one decode call. Each frame draws its code class (n, R, u)
+# uniformly from the grid below and its QBER from U[qber_lo, qber_hi]; the column degrees follow the n=65536
+# rate-0.7 workload's distribution at every size and rate, m = round(n (1 - R)) per matrix.
+UNEVEN_SIZES = (1 << 14, 1 << 16, 1 << 18)
+UNEVEN_RATES = (0.5, 0.6, 0.7, 0.8)
+UNEVEN_US = (2, 3)
+UNEVEN_DIST = {2: 0.3, 3: 0.4, 8: 0.3}
+
+
+def uneven_batch(frames: int, seed: int, sizes=UNEVEN_SIZES, rates=UNEVEN_RATES, us=UNEVEN_US,
+                 qber=(0.01, 0.04)) -> list[dict]:
+    """Group specs of an uneven batch: one dict per (n, R, u) class with its code parameters
+    (n, m, dist, u, cfg_seed), the number of frames that drew it and their QBERs (float64 array)."""
+    classes = [(n, r, u) for n in sizes for r in rates for u in us]
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 0xBA7C])))
+    cls = rng.integers(0, len(classes), size=frames)
+    e = rng.uniform(qber[0], qber[1], size=frames)
+    groups = []
+    for k, (n, r, u) in enumerate(classes):
+        idx = np.flatnonzero(cls == k)
+        groups.append(dict(n=n, m=int(round(n * (1.0 - r))), dist=dict(UNEVEN_DIST), u=u, rate=r,
+                           cfg_seed=int(seed) * 100 + k, frames=int(idx.size), qber=e[idx].copy()))
+    return groups

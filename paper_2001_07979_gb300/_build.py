@@ -13,8 +13,9 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmbp.so")
 
-SOURCES = ["mbp_api.cpp", "mbp_kernels.cu", "mbp_resident.cu", "mbp_stream_f32.cu", "mbp_stream_f64.cu",
-           "mbp_stream_f16.cu", "mbp_stream_bf16.cu"]
+SOURCES = ["mbp_api.cpp", "mbp_kernels.cu", "mbp_resident_f32.cu", "mbp_resident_f64.cu", "mbp_stream_f32.cu", "mbp_stream_f64.cu",
+           "mbp_stream_f16.cu", "mbp_stream_bf16.cu", "mbp_multi.cpp", "mbp_multi_f32.cu", "mbp_multi_f16.cu",
+           "mbp_multi_bf16.cu", "mbp_nbp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

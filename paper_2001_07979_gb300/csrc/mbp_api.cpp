@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "mbp_internal.h"
+#include "mbp_nbp.h"
 
 namespace mbp {
 
@@ -137,13 +137,58 @@ int validate_opts(const mbp_opts* o) {
   REQUIRE(std::isfinite(o->l_max) && o->l_max > 0, "l_max must be finite and > 0");
   REQUIRE(o->accumulate == MBP_ACC_AUTO || o->accumulate == MBP_ACC_FLOAT || o->accumulate == MBP_ACC_FIXED,
           "unknown accumulate mode %d", o->accumulate);
-  REQUIRE(o->schedule == MBP_SCHED_AUTO || o->schedule == MBP_SCHED_STREAMING || o->schedule == MBP_SCHED_RESIDENT,
+  REQUIRE(o->schedule == MBP_SCHED_AUTO || o->schedule == MBP_SCHED_STREAMING || o->schedule == MBP_SCHED_RESIDENT ||
+              o->schedule == MBP_SCHED_GRAPH,
           "unknown schedule %d", o->schedule);
+  REQUIRE(o->rule == MBP_RULE_SUM_PRODUCT || o->rule == MBP_RULE_MIN_SUM, "unknown check rule %d", o->rule);
+  REQUIRE(o->update == MBP_UPDATE_FLOODING || o->update == MBP_UPDATE_MATRIX_SERIAL, "unknown update order %d",
+          o->update);
+  if (o->rule != MBP_RULE_SUM_PRODUCT || o->update != MBP_UPDATE_FLOODING) {
+    if (o->schedule != MBP_SCHED_AUTO && o->schedule != MBP_SCHED_STREAMING)
+      return set_error(MBP_EUNSUPPORTED, "the min-sum rule and the matrix-serial order run the streaming schedule");
+    if (o->accumulate == MBP_ACC_FIXED)
+      return set_error(MBP_EUNSUPPORTED, "the min-sum rule and the matrix-serial order accumulate in floating point");
+    if (o->rule == MBP_RULE_MIN_SUM && o->msg_dtype == MBP_MSG_F64)
+      return set_error(MBP_EUNSUPPORTED, "the min-sum rule runs with FP32, FP16 or BF16 messages");
+  }
+  if (o->schedule == MBP_SCHED_GRAPH) return multi_check_opts(o);
   return MBP_OK;
 }
 
+// The single group of a single-code decode under MBP_SCHED_GRAPH (pointers filled in by the caller).
+mbp_group one_group(const mbp_codes* c, int F) {
+  mbp_group g;
+  std::memset(&g, 0, sizeof g);
+  g.codes = c;
+  g.F = F;
+  return g;
+}
+
+int single_workspace(const mbp_codes* c, int F, const mbp_opts* o, bool host_io, size_t* need) {
+  if (o->schedule != MBP_SCHED_GRAPH) {
+    *need = workspace_bytes(c->d, F, o->msg_dtype, host_io);
+    return MBP_OK;
+  }
+  const mbp_group g = one_group(c, F);
+  return multi_workspace(&g, 1, o, host_io, need);
+}
+
+// The decoder state of a single-code decode inside its workspace.
+int single_state(const mbp_codes* c, int F, const mbp_opts* o, bool host_io, void* ws, DevState* st) {
+  if (o->schedule != MBP_SCHED_GRAPH) {
+    carve_workspace(c->d, F, o->msg_dtype, host_io, ws, st);
+    return MBP_OK;
+  }
+  const mbp_group g = one_group(c, F);
+  mbp_opts oo = *o;
+  oo.workspace = ws;
+  return multi_group_state(&g, 1, 0, &oo, host_io, st);
+}
+
 int check_workspace(const mbp_codes* c, int F, const mbp_opts* o) {
-  size_t need = workspace_bytes(c->d, F, o->msg_dtype, o->host_io != 0);
+  size_t need = 0;
+  int rc = single_workspace(c, F, o, o->host_io != 0, &need);
+  if (rc) return rc;
   REQUIRE(o->workspace, "opts->workspace is NULL (size it with mbp_decode_workspace_size)");
   REQUIRE((reinterpret_cast<uintptr_t>(o->workspace) & 255) == 0, "workspace must be 256-byte aligned");
   REQUIRE(o->workspace_bytes >= need, "workspace too small: %zu bytes given, %zu needed", o->workspace_bytes, need);
@@ -239,13 +284,18 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   int32_t max_deg = 0;
   for (int64_t r = 0; r < m_tot; ++r) max_deg = std::max(max_deg, row_deg[r]);
   d.max_row_deg = max_deg;
-  // The decoder visits the stacked rows in degree order (ties keep the stacked
-  // order): row position p owns the slots slice_base[p] .. slice_base[p+1] - 1.
+  // The decoder visits the stacked rows matrix by matrix, each matrix's rows in
+  // degree order (ties keep the stacked order): row position p owns the slots
+  // slice_base[p] .. slice_base[p+1] - 1, and matrix l's rows are the positions
+  // row_pos[l] .. row_pos[l+1] - 1 (the matrix-serial schedule's steps).
   // The order is internal: syndrome bits are looked up through perm_mat /
   // perm_local, and C2V exports go through edge_slot.
   std::vector<int32_t> order(m_tot);
   for (int64_t p = 0; p < m_tot; ++p) order[p] = static_cast<int32_t>(p);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return row_deg[a] < row_deg[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return row_mat[a] != row_mat[b] ? row_mat[a] < row_mat[b] : row_deg[a] < row_deg[b];
+  });
+  for (int l = 0; l <= u; ++l) d.row_pos[l] = d.row_first[l];  // matrices stay in stacked order
   std::vector<uint8_t> perm_mat(std::max<int64_t>(m_tot, 1));
   std::vector<int32_t> perm_local(std::max<int64_t>(m_tot, 1));
   std::vector<int32_t> slice_base(m_tot + 1);
@@ -380,8 +430,7 @@ int mbp_decode_workspace_size(const mbp_codes* codes, int F, const mbp_opts* opt
   REQUIRE(F >= 0, "F must be >= 0");
   int rc = validate_opts(opts);
   if (rc) return rc;
-  *bytes = workspace_bytes(codes->d, F, opts->msg_dtype, opts->host_io != 0);
-  return MBP_OK;
+  return single_workspace(codes, F, opts, opts->host_io != 0, bytes);
 }
 
 static int decode_common(const mbp_codes* codes, int F, const void* llr, const uint32_t* y_bits,
@@ -400,6 +449,19 @@ static int decode_common(const mbp_codes* codes, int F, const void* llr, const u
   REQUIRE_DEV(success, "success");
   if (opts->soft_out) REQUIRE_DEV(opts->soft_out, "opts->soft_out");
   if (opts->synd_ok) REQUIRE_DEV(opts->synd_ok, "opts->synd_ok");
+  if (opts->schedule == MBP_SCHED_GRAPH) {
+    mbp_group g = one_group(codes, F);
+    g.llr = llr;
+    g.y_bits = y_bits;
+    g.qber = qber;
+    g.z_bits = z_bits;
+    g.x_hat_bits = x_hat_bits;
+    g.iters = iters;
+    g.success = success;
+    g.synd_ok = opts->synd_ok;
+    g.soft_out = opts->soft_out;
+    return multi_decode(&g, 1, max_iter, opts, opts->host_io != 0, reinterpret_cast<cudaStream_t>(stream));
+  }
   DevState st;
   carve_workspace(codes->d, F, opts->msg_dtype, opts->host_io != 0, opts->workspace, &st);
   DecodeArgs a{};
@@ -411,6 +473,8 @@ static int decode_common(const mbp_codes* codes, int F, const void* llr, const u
   a.early_exit = opts->early_exit;
   a.accumulate = opts->accumulate;
   a.schedule = opts->schedule;
+  a.rule = opts->rule;
+  a.update = opts->update;
   a.validate = opts->validate;
   a.l_max = opts->l_max;
   a.x_hat_bits = x_hat_bits;
@@ -450,7 +514,7 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   REQUIRE(opts->synd_ok == nullptr || is_device_ptr(opts->synd_ok), "opts->synd_ok must be a device pointer");
   const DevCode& d = codes->d;
   DevState st;
-  carve_workspace(d, F, opts->msg_dtype, true, opts->workspace, &st);
+  if ((rc = single_state(codes, F, opts, true, opts->workspace, &st))) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t wn = (size_t(d.n) + 31) / 32;
   size_t zw = 0;
@@ -469,6 +533,8 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   a.early_exit = opts->early_exit;
   a.accumulate = opts->accumulate;
   a.schedule = opts->schedule;
+  a.rule = opts->rule;
+  a.update = opts->update;
   a.validate = opts->validate;
   a.l_max = opts->l_max;
   a.x_hat_bits = st.io_xhat;
@@ -476,7 +542,20 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   a.success = st.io_success;
   a.soft_out = opts->soft_out;
   a.synd_ok = opts->synd_ok;
-  rc = decode(d, st, opts->msg_dtype, a, s);
+  if (opts->schedule == MBP_SCHED_GRAPH) {
+    mbp_group g = one_group(codes, F);
+    g.y_bits = st.io_y;
+    g.qber = st.io_qber;
+    g.z_bits = st.io_z;
+    g.x_hat_bits = st.io_xhat;
+    g.iters = st.io_iters;
+    g.success = st.io_success;
+    g.synd_ok = opts->synd_ok;
+    g.soft_out = opts->soft_out;
+    rc = multi_decode(&g, 1, max_iter, opts, true, s);
+  } else {
+    rc = decode(d, st, opts->msg_dtype, a, s);
+  }
   if (rc) return rc;
   CK(cudaMemcpyAsync(x_hat_bits, st.io_xhat, size_t(F) * wn * 4, cudaMemcpyDeviceToHost, s), "copy x_hat to host");
   CK(cudaMemcpyAsync(iters, st.io_iters, size_t(F) * 4, cudaMemcpyDeviceToHost, s), "copy iters to host");
@@ -497,6 +576,8 @@ int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits,
   int rc = validate_opts(opts);
   if (rc) return rc;
   REQUIRE(opts->host_io == 0, "opts->host_io must be 0 for mbp_decode_bsc_static");
+  if (opts->schedule == MBP_SCHED_GRAPH)  // instantiating a CUDA graph may allocate
+    return set_error(MBP_EUNSUPPORTED, "mbp_decode_bsc_static runs the streaming or resident schedule only");
   const size_t need = workspace_bytes(codes->d, F, opts->msg_dtype, false);
   REQUIRE(need <= MBP_STATIC_SCRATCH_BYTES,
           "F = %d needs %zu bytes of decoder state, more than the %u bytes of static scratch", F, need,
@@ -523,6 +604,8 @@ int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits,
   a.early_exit = opts->early_exit;
   a.accumulate = opts->accumulate;
   a.schedule = opts->schedule;
+  a.rule = opts->rule;
+  a.update = opts->update;
   a.validate = 0;
   a.l_max = opts->l_max;
   a.x_hat_bits = x_hat_bits;
@@ -544,10 +627,147 @@ int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int fram
   if (rc) return rc;
   REQUIRE_DEV(c2v_out, "c2v_out");
   DevState st;
-  carve_workspace(codes->d, F, opts->msg_dtype, opts->host_io != 0, opts->workspace, &st);
+  if ((rc = single_state(codes, F, opts, opts->host_io != 0, opts->workspace, &st))) return rc;
   cudaError_t e = launch_export_c2v(codes->d, st, opts->msg_dtype, frame, c2v_out,
                                     reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? MBP_OK : cuda_error(e, "export kernel");
+}
+
+static int check_groups(const mbp_group* g, int G, const mbp_opts* o, bool need_workspace) {
+  REQUIRE(G >= 0 && G <= kMaxGroups, "G = %d outside [0, %d]", G, kMaxGroups);
+  REQUIRE(G == 0 || g, "groups is NULL");
+  int rc = validate_opts(o);
+  if (rc) return rc;
+  if ((rc = multi_check_opts(o))) return rc;
+  int64_t tiles = 0;
+  for (int i = 0; i < G; ++i) {
+    REQUIRE(g[i].codes, "group %d: codes is NULL", i);
+    REQUIRE(g[i].F >= 0, "group %d: F must be >= 0", i);
+    tiles += (g[i].F + kLanes - 1) / kLanes;
+  }
+  if (tiles > 65535) return set_error(MBP_EUNSUPPORTED, "a batch may hold at most %d frames", 65535 * kLanes);
+  if (!need_workspace) return MBP_OK;
+  for (int i = 0; i < G; ++i) {
+    if (g[i].F == 0) continue;
+    if (g[i].llr) {
+      REQUIRE(is_device_ptr(g[i].llr), "group %d: llr must be a device pointer", i);
+    } else {
+      REQUIRE(is_device_ptr(g[i].y_bits) && is_device_ptr(g[i].qber),
+              "group %d: y_bits and qber must be device pointers when llr is NULL", i);
+    }
+    REQUIRE(is_device_ptr(g[i].z_bits), "group %d: z_bits must be a device pointer", i);
+    REQUIRE(is_device_ptr(g[i].x_hat_bits), "group %d: x_hat_bits must be a device pointer", i);
+    REQUIRE(is_device_ptr(g[i].iters), "group %d: iters must be a device pointer", i);
+    REQUIRE(is_device_ptr(g[i].success), "group %d: success must be a device pointer", i);
+    REQUIRE(!g[i].synd_ok || is_device_ptr(g[i].synd_ok), "group %d: synd_ok must be a device pointer", i);
+    REQUIRE(!g[i].soft_out || is_device_ptr(g[i].soft_out), "group %d: soft_out must be a device pointer", i);
+  }
+  size_t need = 0;
+  if ((rc = multi_workspace(g, G, o, false, &need))) return rc;
+  REQUIRE(o->workspace, "opts->workspace is NULL (size it with mbp_multi_workspace_size)");
+  REQUIRE((reinterpret_cast<uintptr_t>(o->workspace) & 255) == 0, "workspace must be 256-byte aligned");
+  REQUIRE(o->workspace_bytes >= need, "workspace too small: %zu bytes given, %zu needed", o->workspace_bytes, need);
+  REQUIRE_DEV(o->workspace, "workspace");
+  return MBP_OK;
+}
+
+int mbp_multi_workspace_size(const mbp_group* groups, int G, const mbp_opts* opts, size_t* bytes) {
+  g_err.clear();
+  REQUIRE(bytes, "bytes is NULL");
+  int rc = check_groups(groups, G, opts, false);
+  if (rc) return rc;
+  return multi_workspace(groups, G, opts, false, bytes);
+}
+
+int mbp_decode_multi(const mbp_group* groups, int G, int max_iter, const mbp_opts* opts, mbp_stream_t stream) {
+  g_err.clear();
+  REQUIRE(max_iter >= 0 && max_iter <= 1000000, "max_iter must be in [0, 1e6]");
+  int rc = check_groups(groups, G, opts, true);
+  if (rc) return rc;
+  return multi_decode(groups, G, max_iter, opts, false, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mbp_autotune_multi(const mbp_group* groups, int G, int max_iter, const mbp_opts* opts, mbp_tuning* best,
+                       mbp_stream_t stream) {
+  g_err.clear();
+  REQUIRE(max_iter >= 0 && max_iter <= 1000000, "max_iter must be in [0, 1e6]");
+  int rc = check_groups(groups, G, opts, true);
+  if (rc) return rc;
+  return multi_autotune(groups, G, max_iter, opts, best, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mbp_release_cached(void) {
+  g_err.clear();
+  multi_release();
+  return MBP_OK;
+}
+
+static int check_nbp(const mbp_codes* codes, int F, int T, double l_max, const void* ws, size_t ws_bytes) {
+  REQUIRE(codes, "codes is NULL");
+  REQUIRE(F >= 0 && T >= 1 && T <= 1000, "F must be >= 0 and T in [1, 1000]");
+  REQUIRE(std::isfinite(l_max) && l_max > 0, "l_max must be finite and > 0");
+  if (codes->d.max_row_deg > 32)
+    return set_error(MBP_EUNSUPPORTED, "the unrolled decoder supports checks of at most 32 edges");
+  if (F == 0) return MBP_OK;
+  if ((F + kLanes - 1) / kLanes > 65535) return set_error(MBP_EUNSUPPORTED, "F = %d is too large", F);
+  const size_t need = nbp_workspace_bytes(codes->d, F, T);
+  REQUIRE(ws, "workspace is NULL (size it with mbp_nbp_workspace_size)");
+  REQUIRE((reinterpret_cast<uintptr_t>(ws) & 255) == 0, "workspace must be 256-byte aligned");
+  REQUIRE(ws_bytes >= need, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+  REQUIRE_DEV(ws, "workspace");
+  return MBP_OK;
+}
+
+int mbp_nbp_workspace_size(const mbp_codes* codes, int F, int T, size_t* bytes) {
+  g_err.clear();
+  REQUIRE(codes && bytes, "codes and bytes must be non-NULL");
+  REQUIRE(F >= 0 && T >= 1 && T <= 1000, "F must be >= 0 and T in [1, 1000]");
+  *bytes = nbp_workspace_bytes(codes->d, F, T);
+  return MBP_OK;
+}
+
+int mbp_nbp_forward(const mbp_codes* codes, int F, int T, const float* llr, const uint32_t* z_bits,
+                    const float* alpha, const float* beta, double l_max, void* workspace, size_t workspace_bytes,
+                    float* lv_out, mbp_stream_t stream) {
+  g_err.clear();
+  int rc = check_nbp(codes, F, T, l_max, workspace, workspace_bytes);
+  if (rc || F == 0) return rc;
+  REQUIRE_DEV(llr, "llr");
+  REQUIRE_DEV(z_bits, "z_bits");
+  REQUIRE_DEV(alpha, "alpha");
+  REQUIRE_DEV(beta, "beta");
+  if (lv_out) REQUIRE_DEV(lv_out, "lv_out");
+  DevState st;
+  NbpState ns;
+  nbp_carve(codes->d, F, T, workspace, &st, &ns);
+  return nbp_forward(codes->d, st, ns, llr, z_bits, alpha, beta, l_max, lv_out,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mbp_nbp_backward(const mbp_codes* codes, int F, int T, const float* alpha, const float* beta, double l_max,
+                     const float* grad_lv, void* workspace, size_t workspace_bytes, float* grad_alpha,
+                     float* grad_beta, float* grad_llr, mbp_stream_t stream) {
+  g_err.clear();
+  int rc = check_nbp(codes, F, T, l_max, workspace, workspace_bytes);
+  if (rc) return rc;
+  REQUIRE_DEV(grad_alpha, "grad_alpha");
+  REQUIRE_DEV(grad_beta, "grad_beta");
+  if (F == 0) {
+    const size_t b = sizeof(float) * size_t(T) * codes->d.u;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(grad_alpha, 0, b, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad_beta, 0, b, s);
+    return e == cudaSuccess ? MBP_OK : cuda_error(e, "clear gradients");
+  }
+  REQUIRE_DEV(alpha, "alpha");
+  REQUIRE_DEV(beta, "beta");
+  REQUIRE_DEV(grad_lv, "grad_lv");
+  if (grad_llr) REQUIRE_DEV(grad_llr, "grad_llr");
+  DevState st;
+  NbpState ns;
+  nbp_carve(codes->d, F, T, workspace, &st, &ns);
+  return nbp_backward(codes->d, ns, alpha, beta, l_max, grad_lv, grad_alpha, grad_beta, grad_llr,
+                      reinterpret_cast<cudaStream_t>(stream));
 }
 
 int mbp_profile_enable(int on) {

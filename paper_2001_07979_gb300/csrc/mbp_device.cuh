@@ -171,6 +171,20 @@ __device__ __forceinline__ void st_msg(T* p, T v) {
   else __stcs(p, v);
 }
 
+// Channel LLR L_P of one node for this lane. BSC inputs keep Bob's bits as one
+// word per node (bit = lane) and ln((1 - e)/e) per lane, so L_P = (1 - 2y) mag
+// (eq. 5) costs a 4-byte broadcast load instead of a 128-byte vector; general
+// inputs keep the LLR array (yt == NULL). tn = tile * n + node.
+template <typename M, int POL>
+__device__ __forceinline__ M channel_llr(const M* __restrict__ lp, const uint32_t* __restrict__ yt,
+                                         const M* __restrict__ ymag, int64_t tn, int tile, int lane) {
+  if (yt) {
+    const M m = ld_state<POL>(ymag + tile * kLanes + lane);
+    return ((ld_state<POL>(yt + tn) >> lane) & 1u) ? -m : m;
+  }
+  return ld_state<POL>(lp + tn * kLanes + lane);
+}
+
 // ------------------------------------------------------------- eq. (6)
 
 // The check-node update of eq. (6) for one row and one lane (frame).
@@ -183,6 +197,10 @@ __device__ __forceinline__ void st_msg(T* p, T v) {
 // of the V2C words' top bits, and each edge's own sign is kept in the sign bit
 // of its delta, whose magnitude the (+) operations read through |.|.
 //
+// ysrc != NULL: the first iteration of BSC inputs, where V2C = L_P comes from
+// the sign words ysrc (bit = lane) and this lane's magnitude ymag instead of
+// gsrc (a warp-uniform branch at the loads; the arithmetic is shared).
+//
 // FIXED: also add each edge's change of message, q(C2V_new) - q(C2V_old) with
 // q(x) = round(x * qscale), to the posterior accumulator lacc of its variable
 // node (a 32-bit red.global.add in L2). Integer addition is associative, so
@@ -190,14 +208,22 @@ __device__ __forceinline__ void st_msg(T* p, T v) {
 // the atomics; finalize_kernel turns it into L_V.
 template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL>
 __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, const M* __restrict__ gsrc,
-                                       S* __restrict__ msg, int first_iter, uint32_t par, bool store, M l_max,
-                                       M inv_l_max, int32_t* __restrict__ lacc, float qscale) {
+                                       const uint32_t* __restrict__ ysrc, M ymag, S* __restrict__ msg,
+                                       int first_iter, uint32_t par, bool store, M l_max, M inv_l_max,
+                                       int32_t* __restrict__ lacc, float qscale) {
   int col[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : -1;
   M v[D];
+  if (ysrc) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : M(0);
+    for (int k = 0; k < D; ++k)
+      v[k] = (!CHECKED || col[k] >= 0) ? (((ld_state<POL>(ysrc + col[k]) >> lane) & 1u) ? -ymag : ymag) : M(0);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : M(0);
+  }
   [[maybe_unused]] M old[FIXED ? D : 1];
   if (!first_iter) {
 #pragma unroll
@@ -241,32 +267,152 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
 }
 
 // Check row p (degree order) of one tile, by one warp. Rows of exactly DMAX or
-// DMAX - 1 edges take an unchecked body.
+// DMAX - 1 edges take an unchecked body. lsrc is the posterior (L_P in the
+// first iteration of general inputs); the first iteration of BSC inputs reads
+// the sign words yt and magnitudes ymag instead.
+template <typename M, typename S, int DMAX, bool FIXED, int POL>
+__device__ __forceinline__ void cn_tile_row_src(int deg, const int* __restrict__ cols,
+                                                const M* __restrict__ gsrc, const uint32_t* __restrict__ ysrc,
+                                                M ym, S* __restrict__ msg, int first_iter, uint32_t par,
+                                                bool store, M l_max, M inv_l_max, int32_t* __restrict__ lacc,
+                                                float qscale) {
+  if (deg == DMAX)
+    cn_row<M, S, DMAX, FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, inv_l_max,
+                                       lacc, qscale);
+  else if (DMAX > 1 && deg == DMAX - 1)
+    cn_row<M, S, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par,
+                                                             store, l_max, inv_l_max, lacc, qscale);
+  else
+    cn_row<M, S, DMAX, FIXED, true, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, inv_l_max,
+                                      lacc, qscale);
+}
+
+// The min-sum check rule (an algorithm variant) for one row and one lane, FP32
+// arithmetic: V2C clipped to l_max as for eq. (6), then every edge gets the sign
+// of the others (and z_j) and the smallest magnitude among the others, found
+// from the row's two smallest magnitudes. Padding edges take no part.
+template <typename S, int D, bool CHECKED, int POL>
+__device__ __forceinline__ void cn_row_minsum(int deg, const int* __restrict__ cols, const float* __restrict__ gsrc,
+                                              const uint32_t* __restrict__ ysrc, float ymag, S* __restrict__ msg,
+                                              int first_iter, uint32_t par, bool store, float l_max) {
+  int col[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : -1;
+  float v[D];
+  if (ysrc) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      v[k] = (!CHECKED || col[k] >= 0) ? (((ld_state<POL>(ysrc + col[k]) >> lane) & 1u) ? -ymag : ymag) : 0.f;
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : 0.f;
+  }
+  if (!first_iter) {
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      v[k] -= (!CHECKED || col[k] >= 0) ? float(Store<S>::widen(ld_msg<POL>(msg + k * kLanes))) : 0.f;
+  }
+  float m1 = __int_as_float(0x7f800000), m2 = m1;  // +inf
+  int i1 = -1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    par ^= Bits<float>::sign_word(v[k]);
+    const float a = (!CHECKED || col[k] >= 0) ? fminf(fabsf(v[k]), l_max) : __int_as_float(0x7f800000);
+    if (a < m1) {
+      m2 = m1;
+      m1 = a;
+      i1 = k;
+    } else if (a < m2) {
+      m2 = a;
+    }
+  }
+  if (!store) return;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (!CHECKED || col[k] >= 0) {
+      const float mag = fminf(k == i1 ? m2 : m1, l_max);
+      st_msg<POL>(msg + k * kLanes, Store<S>::narrow(Bits<float>::copy_sign(mag, par ^ Bits<float>::sign_word(v[k]))));
+    }
+}
+
+// One tile's arrays for the check-node update of its rows: pointers offset to
+// the tile (and to this lane where the data is per frame).
+template <typename M, typename S>
+struct CnView {
+  const int32_t* slice_base;
+  const int32_t* slot_col;
+  S* msg;                // the tile's messages, lane
+  const M* gsrc;         // the tile's posterior (or L_P), lane
+  const uint32_t* ysrc;  // the tile's sign words in the first iteration of BSC inputs, else NULL
+  M ym;                  // this lane's ln((1 - e)/e) with ysrc
+  const uint32_t* zt;    // the tile's syndrome words
+  int32_t* lacc;         // the tile's fixed-point sums, lane (FIXED) or NULL
+  uint32_t act;          // lanes still decoding
+};
+
+template <typename M, typename S, int POL>
+__device__ __forceinline__ CnView<M, S> cn_view(const DevCode& c, int tile, uint32_t act, int first_iter,
+                                                S* __restrict__ c2v, const M* __restrict__ lsrc,
+                                                const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
+                                                const uint32_t* __restrict__ zt, int32_t* __restrict__ lacc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
+  const bool signs = first_iter && yt;
+  CnView<M, S> v;
+  v.slice_base = c.slice_base;
+  v.slot_col = c.slot_col;
+  v.msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
+  v.gsrc = lsrc + node0;
+  v.ysrc = signs ? yt + int64_t(tile) * c.n : nullptr;
+  v.ym = signs ? ld_state<POL>(ymag + tile * kLanes + lane) : M(0);
+  v.zt = zt + int64_t(tile) * c.m_tot;
+  v.lacc = lacc ? lacc + node0 : nullptr;
+  v.act = act;
+  return v;
+}
+
+// Check row p (degree order) of the view's tile, by one warp.
+template <typename M, typename S, int DMAX, bool FIXED, int POL>
+__device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int first_iter, M l_max, M inv_l_max,
+                                            float qscale) {
+  const int lane = threadIdx.x & 31;
+  const int base = v.slice_base[p];
+  const int deg = v.slice_base[p + 1] - base;
+  const uint32_t par = ((v.zt[p] >> lane) & 1u) << 31;
+  const bool store = (v.act >> lane) & 1u;
+  cn_tile_row_src<M, S, DMAX, FIXED, POL>(deg, v.slot_col + base, v.gsrc, v.ysrc, v.ym,
+                                          v.msg + int64_t(base) * kLanes, first_iter, par, store, l_max, inv_l_max,
+                                          v.lacc, qscale);
+}
+
+// Min-sum rule for check row p of the view's tile (FP32 arithmetic).
+template <typename S, int DMAX, int POL>
+__device__ __forceinline__ void cn_view_row_minsum(const CnView<float, S>& v, int p, int first_iter, float l_max) {
+  const int lane = threadIdx.x & 31;
+  const int base = v.slice_base[p];
+  const int deg = v.slice_base[p + 1] - base;
+  const uint32_t par = ((v.zt[p] >> lane) & 1u) << 31;
+  const bool store = (v.act >> lane) & 1u;
+  const int* cols = v.slot_col + base;
+  S* msg = v.msg + int64_t(base) * kLanes;
+  if (deg == DMAX)
+    cn_row_minsum<S, DMAX, false, POL>(deg, cols, v.gsrc, v.ysrc, v.ym, msg, first_iter, par, store, l_max);
+  else if (DMAX > 1 && deg == DMAX - 1)
+    cn_row_minsum<S, (DMAX > 1 ? DMAX - 1 : 1), false, POL>(deg, cols, v.gsrc, v.ysrc, v.ym, msg, first_iter, par,
+                                                            store, l_max);
+  else
+    cn_row_minsum<S, DMAX, true, POL>(deg, cols, v.gsrc, v.ysrc, v.ym, msg, first_iter, par, store, l_max);
+}
+
 template <typename M, typename S, int DMAX, bool FIXED, int POL>
 __device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, uint32_t act, int first_iter,
                                             S* __restrict__ c2v, const M* __restrict__ lsrc,
+                                            const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                             const uint32_t* __restrict__ zt, M l_max, M inv_l_max,
                                             int32_t* __restrict__ lacc, float qscale) {
-  const int lane = threadIdx.x & 31;
-  const int base = c.slice_base[p];
-  const int deg = c.slice_base[p + 1] - base;
-  const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
-  S* msg = c2v + (int64_t(tile) * c.s_tot + base) * kLanes + lane;  // edge k at msg[k * kLanes]
-  const M* gsrc = lsrc + node0;                                     // node i at gsrc[i * kLanes]
-  int32_t* lacc_lane = FIXED ? lacc + node0 : nullptr;
-  const int* cols = c.slot_col + base;
-  const uint32_t zw = zt[int64_t(tile) * c.m_tot + p];
-  const uint32_t par = ((zw >> lane) & 1u) << 31;
-  const bool store = (act >> lane) & 1u;
-  if (deg == DMAX)
-    cn_row<M, S, DMAX, FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
-                                       qscale);
-  else if (DMAX > 1 && deg == DMAX - 1)
-    cn_row<M, S, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max,
-                                                             inv_l_max, lacc_lane, qscale);
-  else
-    cn_row<M, S, DMAX, FIXED, true, POL>(deg, cols, gsrc, msg, first_iter, par, store, l_max, inv_l_max, lacc_lane,
-                                      qscale);
+  const CnView<M, S> v = cn_view<M, S, POL>(c, tile, act, first_iter, c2v, lsrc, yt, ymag, zt, FIXED ? lacc : nullptr);
+  cn_view_row<M, S, DMAX, FIXED, POL>(v, p, first_iter, l_max, inv_l_max, qscale);
 }
 
 // ------------------------------------------------------------- eq. (2)
@@ -289,32 +435,72 @@ __device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const 
   return sum;
 }
 
-// The variable-node update of node `col` of one tile, by one warp: the soft
-// decision L_V = L_P + sum of the node's C2V over all matrices (eq. 2) and the
-// hard decision, whose 32 lanes are one word of xh. Nodes with more than 16
+// One tile's arrays for the variable-node update of its nodes.
+template <typename M, typename S>
+struct VnView {
+  const int32_t* col_ptr;
+  const int32_t* col_slot;
+  const S* msg;          // the tile's messages, lane
+  M* lv;                 // the tile's posteriors, lane
+  const M* lp;           // the tile's L_P (general inputs), lane
+  const uint32_t* yt;    // the tile's sign words (BSC inputs) or NULL
+  M ym;                  // this lane's ln((1 - e)/e) with yt
+  uint32_t* xh;          // the tile's decision words
+  uint32_t act;
+};
+
+template <typename M, typename S, int POL>
+__device__ __forceinline__ VnView<M, S> vn_view(const DevCode& c, int tile, uint32_t act, const S* __restrict__ c2v,
+                                                M* __restrict__ lv, const M* __restrict__ lp,
+                                                const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
+                                                uint32_t* __restrict__ xh) {
+  const int lane = threadIdx.x & 31;
+  const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
+  VnView<M, S> v;
+  v.col_ptr = c.col_ptr;
+  v.col_slot = c.col_slot;
+  v.msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
+  v.lv = lv + node0;
+  v.lp = lp + node0;
+  v.yt = yt ? yt + int64_t(tile) * c.n : nullptr;
+  v.ym = yt ? ld_state<POL>(ymag + tile * kLanes + lane) : M(0);
+  v.xh = xh + int64_t(tile) * c.n;
+  v.act = act;
+  return v;
+}
+
+// The variable-node update of node `col` of the view's tile, by one warp: the
+// soft decision L_V = L_P + sum of the node's C2V over all matrices (eq. 2) and
+// the hard decision, whose 32 lanes are one word of xh. Nodes with more than 16
 // edges are summed 16 edges at a time, still in stacked-row order.
+template <typename M, typename S, int POL>
+__device__ __forceinline__ void vn_view_node(const VnView<M, S>& v, int col) {
+  const int lane = threadIdx.x & 31;
+  const int a0 = v.col_ptr[col];
+  const int d = v.col_ptr[col + 1] - a0;
+  const int* slots = v.col_slot + a0;
+  M sum;
+  if (v.yt) sum = ((ld_state<POL>(v.yt + col) >> lane) & 1u) ? -v.ym : v.ym;
+  else sum = ld_state<POL>(v.lp + int64_t(col) * kLanes);
+  if (d <= 4) sum = vn_sum<M, S, 4, POL>(slots, d, v.msg, sum);
+  else if (d <= 8) sum = vn_sum<M, S, 8, POL>(slots, d, v.msg, sum);
+  else
+    for (int b = 0; b < d; b += 16) sum = vn_sum<M, S, 16, POL>(slots + b, d - b, v.msg, sum);
+  if ((v.act >> lane) & 1u) v.lv[int64_t(col) * kLanes] = sum;
+  const uint32_t hard = __ballot_sync(kFull, sum < M(0));
+  if (lane == 0) {
+    uint32_t* px = v.xh + col;
+    const uint32_t prev = ld_state<POL>(px);
+    *px = (prev & ~v.act) | (hard & v.act);
+  }
+}
+
 template <typename M, typename S, int POL>
 __device__ __forceinline__ void vn_node(const DevCode& c, int tile, int col, uint32_t act,
                                         const S* __restrict__ c2v, M* __restrict__ lv, const M* __restrict__ lp,
+                                        const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                         uint32_t* __restrict__ xh) {
-  const int lane = threadIdx.x & 31;
-  const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
-  const S* msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
-  const int a0 = c.col_ptr[col];
-  const int d = c.col_ptr[col + 1] - a0;
-  const int* slots = c.col_slot + a0;
-  M sum = lp[at];
-  if (d <= 4) sum = vn_sum<M, S, 4, POL>(slots, d, msg, sum);
-  else if (d <= 8) sum = vn_sum<M, S, 8, POL>(slots, d, msg, sum);
-  else
-    for (int b = 0; b < d; b += 16) sum = vn_sum<M, S, 16, POL>(slots + b, d - b, msg, sum);
-  if ((act >> lane) & 1u) lv[at] = sum;
-  const uint32_t hard = __ballot_sync(kFull, sum < M(0));
-  if (lane == 0) {
-    uint32_t* px = xh + int64_t(tile) * c.n + col;
-    const uint32_t prev = ld_state<POL>(px);
-    *px = (prev & ~act) | (hard & act);
-  }
+  vn_view_node<M, S, POL>(vn_view<M, S, POL>(c, tile, act, c2v, lv, lp, yt, ymag, xh), col);
 }
 
 // ------------------------------------------------------- stopping rule

@@ -3,7 +3,8 @@
 // Device layout of the stacked code [H_1; ...; H_u] (Section 2: u matrices of
 // size m_l x n sharing the n variable nodes):
 //   * stacked row r = row_first[l] + j is row j of H_l (the CSR arrays);
-//   * for the decoder the rows are put in degree order (position p); the row at
+//   * for the decoder the rows are put in (matrix, degree) order (position p;
+//     matrix l's rows are positions row_pos[l] .. row_pos[l+1] - 1); the row at
 //     position p owns the edge "slots" slice_base[p] .. slice_base[p+1] - 1,
 //     slot slice_base[p] + k holding its edge k (column slot_col); row_mat and
 //     row_local name the matrix and row of each position;
@@ -39,7 +40,8 @@ struct DevCode {
   int32_t max_col_deg;
   int64_t e_tot, s_tot;
   int32_t m[kMaxU];
-  int32_t row_first[kMaxU + 1];
+  int32_t row_first[kMaxU + 1];  // first stacked row of each matrix (CSR order)
+  int32_t row_pos[kMaxU + 1];    // first row position of each matrix (the decoder's order)
   const int32_t* slice_base;  // [m_tot + 1] first slot of each row position
   const int32_t* slot_col;    // [s_tot]
   const int32_t* col_ptr;     // [n + 1]
@@ -56,13 +58,14 @@ struct DevState {
   int32_t F, n_tiles;
   void* c2v;          // [n_tiles][s_tot][kLanes] message type
   void* lv;           // [n_tiles][n][kLanes] posterior L_V of eq. (2)
-  void* lp;           // [n_tiles][n][kLanes] channel LLR L_P
+  void* lp;           // [n_tiles][n][kLanes] channel LLR L_P of general (LLR) inputs
+  uint32_t* yt;       // [n_tiles][n] Bob's bits, bit lane, for BSC inputs; NULL when L_P comes from lp
+  void* chan_mag;     // [n_tiles][kLanes] ln((1 - e)/e) per frame (internal unit) for BSC inputs
   int32_t* lacc;      // [n_tiles][n][kLanes] fixed-point sum of C2V per node (FP32 single pass), or NULL
   uint32_t* xh;       // [n_tiles][n] hard decisions, bit lane
   uint32_t* zt;       // [n_tiles][m_tot] syndrome bits, bit lane
   uint32_t* active;   // [n_tiles] lanes still decoding
   uint32_t* fail;     // [n_tiles][u] lanes whose hard decision violates some check of H_l
-  double* llr_mag;    // [F] ln((1 - e)/e) for the BSC entry points
   int32_t* counters;  // [4]: unfinished tiles, non-finite flag
   void* ctl;          // control block of the resident schedule (barrier, retirement)
   // staging for mbp_decode_bsc_host
@@ -105,6 +108,8 @@ struct DecodeArgs {
   int early_exit;
   int accumulate;
   int schedule;
+  int rule;      // MBP_RULE_*: check-node rule
+  int update;    // MBP_UPDATE_*: flooding or matrix by matrix
   int validate;
   double l_max;
   uint32_t* x_hat_bits;
@@ -132,6 +137,9 @@ int static_scratch(void** ptr);
 template <typename M, typename S>
 int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
                       float inv_qscale, cudaStream_t s);
+// one flooding iteration of one group, no host synchronisation (grouped decode; float arithmetic)
+template <typename M, typename S>
+cudaError_t stream_group_step(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s);
 template <typename M>
 int resident_group(const DevCode& c, int n_tiles);
 template <typename M>

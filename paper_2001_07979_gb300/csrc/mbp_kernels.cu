@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "mbp_device.cuh"
+#include "mbp_multi.h"
 
 // Fixed device scratch of mbp_decode_bsc_static: the decoder state of one call,
 // for callers that must not allocate. Every GPU that loads this library holds
@@ -71,23 +72,54 @@ __global__ void bsc_llr_kernel(const uint32_t* __restrict__ y, const double* __r
   llr[int64_t(f) * n + i] = M(bit ? -mag : mag);
 }
 
-// ln((1 - e)/e) per frame in double precision, times `unit` (the decoder's internal LLR unit).
-__global__ void frame_mag_kernel(const double* __restrict__ qber, int F, double unit, double* __restrict__ mag) {
+// ln((1 - e)/e) per frame in double precision, times `unit` (the decoder's
+// internal LLR unit), rounded once to M; one value per (tile, lane), 0 for the
+// lanes past the last frame.
+template <typename M>
+__global__ void chan_mag_kernel(const double* __restrict__ qber, int F, int n_lanes, double unit,
+                                M* __restrict__ mag) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_lanes) return;
+  M v = M(0);
   if (f < F) {
     const double e = qber[f];
-    mag[f] = log((1.0 - e) / e) * unit;
+    v = M(log((1.0 - e) / e) * unit);
   }
+  mag[f] = v;
 }
 
 // ------------------------------------------------------------- set-up
 
-// L_P into the interleaved layout and the hard decision of iteration 0.
-// One warp per (tile, variable node), lane = frame.
+// BSC inputs: Bob's bits into one word per (tile, node) with bit = lane (the
+// sign words of L_P = (1 - 2y) mag, eq. 5), and the hard decision of iteration
+// 0, [L_P < 0] = y where mag > 0. One warp per (tile, 32-node word): lane l
+// reads frame l's word, and a ballot per node transposes it.
 template <typename M>
-__global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr, const uint32_t* __restrict__ y,
-                               const double* __restrict__ mag, M* __restrict__ lp, uint32_t* __restrict__ xh,
-                               int32_t* __restrict__ counters, int validate) {
+__global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ y, const M* __restrict__ mag,
+                                 uint32_t* __restrict__ yt, uint32_t* __restrict__ xh) {
+  const int wn = (c.n + 31) >> 5;
+  const int tile = blockIdx.y;
+  const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w >= wn) return;
+  const int lane = threadIdx.x & 31;
+  const int f = tile * kLanes + lane;
+  const uint32_t yw = f < F ? y[int64_t(f) * wn + w] : 0u;
+  const uint32_t pos = __ballot_sync(kFull, mag[tile * kLanes + lane] > M(0));
+  for (int b = 0; b < 32; ++b) {
+    const uint32_t word = __ballot_sync(kFull, (yw >> b) & 1u);
+    const int i = w * 32 + b;
+    if (lane == b && i < c.n) {
+      yt[int64_t(tile) * c.n + i] = word;
+      xh[int64_t(tile) * c.n + i] = word & pos;
+    }
+  }
+}
+
+// General inputs: L_P into the interleaved layout (internal unit) and the hard
+// decision of iteration 0. One warp per (tile, variable node), lane = frame.
+template <typename M>
+__global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr, M* __restrict__ lp,
+                               uint32_t* __restrict__ xh, int32_t* __restrict__ counters, int validate) {
   const int tile = blockIdx.y;
   const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= c.n) return;
@@ -95,15 +127,9 @@ __global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr
   const int f = tile * kLanes + lane;
   M v = M(0);
   if (f < F) {
-    if (llr) {
-      v = llr[int64_t(f) * c.n + col];
-      if (validate && !isfinite(v)) atomicOr(&counters[1], 1);
-      v = M(double(v) * Arith<M>::kToInternal);
-    } else {
-      const int wn = (c.n + 31) >> 5;
-      const uint32_t bit = (y[int64_t(f) * wn + (col >> 5)] >> (col & 31)) & 1u;
-      v = M(bit ? -mag[f] : mag[f]);
-    }
+    v = llr[int64_t(f) * c.n + col];
+    if (validate && !isfinite(v)) atomicOr(&counters[1], 1);
+    v = M(double(v) * Arith<M>::kToInternal);
   }
   lp[(int64_t(tile) * c.n + col) * kLanes + lane] = v;
   const uint32_t hard = __ballot_sync(kFull, f < F && v < M(0));
@@ -160,12 +186,15 @@ __global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restri
 
 template <typename M>
 __global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv, const M* __restrict__ lp,
+                                const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                 const int32_t* __restrict__ iters, M* __restrict__ out) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= int64_t(F) * c.n) return;
   const int f = int(idx / c.n), i = int(idx % c.n);
-  const int64_t at = (int64_t(f / kLanes) * c.n + i) * kLanes + (f % kLanes);
-  out[idx] = M((iters[f] == 0 ? lp[at] : lv[at]) * Arith<M>::kToLLR);
+  const int tile = f / kLanes, lane = f % kLanes;
+  const int64_t tn = int64_t(tile) * c.n + i;
+  const M v = iters[f] == 0 ? channel_llr<M, kPolStream>(lp, yt, ymag, tn, tile, lane) : lv[tn * kLanes + lane];
+  out[idx] = M(v * Arith<M>::kToLLR);
 }
 
 template <typename M, typename S>
@@ -178,13 +207,68 @@ __global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, in
 
 // ------------------------------------------------------------- driver
 
-template <typename M, typename S>
-int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s) {
+// Channel LLRs, syndrome words and tile state into the workspace (and the
+// non-finite check of validate mode).
+template <typename M>
+int setup_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s) {
   cudaError_t e;
 #define CK(call, what) \
   if ((e = (call)) != cudaSuccess) return cuda_error(e, what)
 #define CKL(what) CK(cudaGetLastError(), what)
   const int F = st.F, NT = st.n_tiles;
+  CK(cudaMemsetAsync(st.counters, 0, 4 * sizeof(int32_t), s), "clear counters");
+  prof_begin(MBP_KERNEL_SETUP, s);
+  if (a.y_bits) {  // BSC inputs: sign words and per-frame magnitudes, no LLR array
+    chan_mag_kernel<M><<<blocks_for(NT * kLanes, 256), 256, 0, s>>>(a.qber, F, NT * kLanes, Arith<M>::kToInternal,
+                                                                   static_cast<M*>(st.chan_mag));
+    CKL("chan_mag_kernel");
+    init_bits_kernel<M><<<dim3(blocks_for((c.n + 31) >> 5, 8), NT), 256, 0, s>>>(
+        c, F, a.y_bits, static_cast<const M*>(st.chan_mag), st.yt, st.xh);
+    CKL("init_bits_kernel");
+  } else {
+    st.yt = nullptr;
+    init_lp_kernel<M><<<dim3(blocks_for(c.n, 8), NT), 256, 0, s>>>(c, F, static_cast<const M*>(a.llr),
+                                                                   static_cast<M*>(st.lp), st.xh, st.counters,
+                                                                   a.validate);
+    CKL("init_lp_kernel");
+  }
+  init_z_kernel<<<blocks_for(int64_t(NT) * c.m_tot, 256), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt);
+  CKL("init_z_kernel");
+  init_tiles_kernel<<<blocks_for(NT, 256), 256, 0, s>>>(F, NT, c.u, st.active, st.fail);
+  CKL("init_tiles_kernel");
+  prof_end(MBP_KERNEL_SETUP, s, a.y_bits ? 4 : 3);
+  if (a.validate) {
+    int32_t host_ctr[4];
+    CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof host_ctr, cudaMemcpyDeviceToHost, s), "read validate flag");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (host_ctr[1]) return set_error(MBP_EINVAL, "llr holds a non-finite value");
+  }
+  return MBP_OK;
+}
+
+// Output bits (and soft values) of the frames of one decode.
+template <typename M>
+int output_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s) {
+  cudaError_t e;
+  const int F = st.F, NT = st.n_tiles;
+  const int wn = (c.n + 31) >> 5;
+  prof_begin(MBP_KERNEL_OUTPUT, s);
+  out_bits_kernel<<<dim3(blocks_for(wn, 8), NT), 256, 0, s>>>(c, F, st.xh, a.x_hat_bits);
+  CKL("out_bits_kernel");
+  if (a.soft_out) {
+    soft_out_kernel<M><<<blocks_for(int64_t(F) * c.n, 256), 256, 0, s>>>(
+        c, F, static_cast<const M*>(st.lv), static_cast<const M*>(st.lp), st.yt, static_cast<const M*>(st.chan_mag),
+        a.iters, static_cast<M*>(a.soft_out));
+    CKL("soft_out_kernel");
+  }
+  prof_end(MBP_KERNEL_OUTPUT, s, a.soft_out ? 2 : 1);
+  return MBP_OK;
+}
+
+template <typename M, typename S>
+int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s) {
+  cudaError_t e;
+  const int NT = st.n_tiles;
   const double l_max = a.l_max * Arith<M>::kToInternal;  // clip in the decoder's internal LLR unit
   // accumulation of eq. (2): fixed-point single pass (FP32 messages) or float two-pass
   int qbits = 0;
@@ -198,28 +282,9 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
                                        " l_max <= 2^%d", 31 - kMinQBits);
   const bool fixed = fixed_ok && a.accumulate == MBP_ACC_FIXED;
   const float qscale = float(std::ldexp(1.0, qbits)), inv_qscale = float(std::ldexp(1.0, -qbits));
-  CK(cudaMemsetAsync(st.counters, 0, 4 * sizeof(int32_t), s), "clear counters");
   if (fixed) CK(cudaMemsetAsync(st.lacc, 0, size_t(NT) * c.n * kLanes * sizeof(int32_t), s), "clear accumulator");
-  const dim3 node_grid(blocks_for(c.n, 8), NT);
-  prof_begin(MBP_KERNEL_SETUP, s);
-  if (a.y_bits) {
-    frame_mag_kernel<<<blocks_for(F, 256), 256, 0, s>>>(a.qber, F, Arith<M>::kToInternal, st.llr_mag);
-    CKL("frame_mag_kernel");
-  }
-  init_lp_kernel<M><<<node_grid, 256, 0, s>>>(c, F, static_cast<const M*>(a.llr), a.y_bits, st.llr_mag,
-                                              static_cast<M*>(st.lp), st.xh, st.counters, a.validate);
-  CKL("init_lp_kernel");
-  init_z_kernel<<<blocks_for(int64_t(NT) * c.m_tot, 256), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt);
-  CKL("init_z_kernel");
-  init_tiles_kernel<<<blocks_for(NT, 256), 256, 0, s>>>(F, NT, c.u, st.active, st.fail);
-  CKL("init_tiles_kernel");
-  prof_end(MBP_KERNEL_SETUP, s, a.y_bits ? 4 : 3);
-  int32_t host_ctr[4];
-  if (a.validate) {
-    CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof host_ctr, cudaMemcpyDeviceToHost, s), "read validate flag");
-    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    if (host_ctr[1]) return set_error(MBP_EINVAL, "llr holds a non-finite value");
-  }
+  int rc = setup_t<M>(c, st, a, s);
+  if (rc) return rc;
   // schedule: resident (one cooperative launch, groups of tiles kept in L2) or streaming (kernels per iteration)
   constexpr bool same_store = sizeof(M) == sizeof(S);
   const int G = (fixed || !same_store || a.schedule != MBP_SCHED_RESIDENT) ? 0 : resident_group<M>(c, NT);
@@ -237,25 +302,15 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (resident_error(ctl_h)) return set_error(MBP_ETIMEOUT, "a grid barrier of the resident schedule timed out");
   } else {
-    const int rc = stream_iterations<M, S>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
+    rc = stream_iterations<M, S>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
     if (rc) return rc;
   }
-  const int wn = (c.n + 31) >> 5;
-  prof_begin(MBP_KERNEL_OUTPUT, s);
-  out_bits_kernel<<<dim3(blocks_for(wn, 8), NT), 256, 0, s>>>(c, F, st.xh, a.x_hat_bits);
-  CKL("out_bits_kernel");
-  if (a.soft_out) {
-    soft_out_kernel<M><<<blocks_for(int64_t(F) * c.n, 256), 256, 0, s>>>(
-        c, F, static_cast<const M*>(st.lv), static_cast<const M*>(st.lp), a.iters, static_cast<M*>(a.soft_out));
-    CKL("soft_out_kernel");
-  }
-  prof_end(MBP_KERNEL_OUTPUT, s, a.soft_out ? 2 : 1);
+  return output_t<M>(c, st, a, s);
 #undef CKL
 #undef CK
-  return MBP_OK;
 }
 
-constexpr int kRegions = 17;
+constexpr int kRegions = 18;
 
 // bytes of one stored message and of one posterior / channel value
 size_t msg_size(int msg_dtype) {
@@ -280,7 +335,7 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
       NT * size_t(c.m_tot) * 4,                                       // zt
       NT * 4,                                                         // active
       NT * size_t(c.u) * 4,                                           // fail
-      size_t(F) * 8,                                                  // llr_mag
+      NT * kLanes * node_size(msg_dtype),                             // chan_mag
       16,                                                             // counters
       64,                                                             // resident schedule control block
       host_io ? size_t(F) * wn * 4 : 0,                               // io_y
@@ -289,6 +344,7 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
       host_io ? size_t(F) * wn * 4 : 0,                               // io_xhat
       host_io ? size_t(F) * 4 : 0,                                    // io_iters
       host_io ? size_t(F) : 0,                                        // io_success
+      NT * size_t(c.n) * 4,                                           // yt
   };
   size_t t = 0;
   for (int i = 0; i < kRegions; ++i) {
@@ -341,7 +397,8 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->zt = reinterpret_cast<uint32_t*>(b + o[5]);
   st->active = reinterpret_cast<uint32_t*>(b + o[6]);
   st->fail = reinterpret_cast<uint32_t*>(b + o[7]);
-  st->llr_mag = reinterpret_cast<double*>(b + o[8]);
+  st->chan_mag = b + o[8];
+  st->yt = reinterpret_cast<uint32_t*>(b + o[17]);
   st->counters = reinterpret_cast<int32_t*>(b + o[9]);
   st->ctl = b + o[10];
   st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;
@@ -351,6 +408,16 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->io_iters = host_io ? reinterpret_cast<int32_t*>(b + o[15]) : nullptr;
   st->io_success = host_io ? reinterpret_cast<uint8_t*>(b + o[16]) : nullptr;
 }
+
+int group_setup(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {
+  return msg_dtype == MBP_MSG_F64 ? setup_t<double>(c, st, a, s) : setup_t<float>(c, st, a, s);
+}
+
+int group_output(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {
+  return msg_dtype == MBP_MSG_F64 ? output_t<double>(c, st, a, s) : output_t<float>(c, st, a, s);
+}
+
+void group_layout(const DevCode& c, int F, int msg_dtype, size_t* bytes) { *bytes = workspace_bytes(c, F, msg_dtype, false); }
 
 int decode(const DevCode& c, DevState& st, int msg_dtype, const DecodeArgs& a, cudaStream_t s) {
   if (st.n_tiles > 65535) return set_error(MBP_EUNSUPPORTED, "F = %d exceeds %d frames per call", st.F, 65535 * kLanes);

@@ -7,6 +7,11 @@
 // stay in L2 from one iteration to the next. The barrier wait is bounded: a
 // block that waits longer than the limit sets ctl->error and every block
 // returns; the host reports MBP_ETIMEOUT.
+//
+// Templates over the message type M, instantiated in mbp_resident_<type>.cu
+// (one file per type so they build in parallel).
+#pragma once
+
 #include <cmath>
 #include <cstdlib>
 
@@ -64,6 +69,7 @@ template <typename M, int DMAX>
 __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, int n_tiles, int G, int max_iter,
                                                        int early_exit, M l_max, M* __restrict__ c2v,
                                                        M* __restrict__ lv, const M* __restrict__ lp,
+                                                       const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                                        uint32_t* __restrict__ xh, const uint32_t* __restrict__ zt,
                                                        uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
                                                        int32_t* __restrict__ iters, uint8_t* __restrict__ success,
@@ -115,14 +121,14 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
         const int tile = g0 + it / c.m_tot;
         const uint32_t act = __ldcg(active + tile);
         if (act)
-          cn_tile_row<M, M, DMAX, false, kPolCoherent>(c, tile, it % c.m_tot, act, t == 1, c2v, lsrc, zt, l_max,
-                                                    inv_l_max, nullptr, 0.f);
+          cn_tile_row<M, M, DMAX, false, kPolCoherent>(c, tile, it % c.m_tot, act, t == 1, c2v, lsrc, yt, ymag, zt,
+                                                    l_max, inv_l_max, nullptr, 0.f);
       }
       if (!grid_sync(ctl, gen, bc)) return;
       for (int it = gw; it < gt * c.n; it += warps) {
         const int tile = g0 + it / c.n;
         const uint32_t act = __ldcg(active + tile);
-        if (act) vn_node<M, M, kPolCoherent>(c, tile, it % c.n, act, c2v, lv, lp, xh);
+        if (act) vn_node<M, M, kPolCoherent>(c, tile, it % c.n, act, c2v, lv, lp, yt, ymag, xh);
       }
       if (!grid_sync(ctl, gen, bc)) return;
       if (early_exit || t == max_iter) {
@@ -148,6 +154,8 @@ cudaError_t launch_resident(const DevCode& c, const DevState& st, const DecodeAr
   M* c2v = static_cast<M*>(st.c2v);
   M* lv = static_cast<M*>(st.lv);
   const M* lp = static_cast<const M*>(st.lp);
+  const uint32_t* yt = st.yt;
+  const M* ymag = static_cast<const M*>(st.chan_mag);
   uint32_t* xh = st.xh;
   const uint32_t* zt = st.zt;
   uint32_t* active = st.active;
@@ -163,16 +171,12 @@ cudaError_t launch_resident(const DevCode& c, const DevState& st, const DecodeAr
   // that never come, and MBP_TEST_BARRIER_TIMEOUT_US shortens the wait limit.
   if (const char* ev = std::getenv("MBP_TEST_BARRIER_EXTRA_ARRIVALS")) bc.arrivals += unsigned(std::atoi(ev));
   if (const char* ev = std::getenv("MBP_TEST_BARRIER_TIMEOUT_US")) bc.timeout = std::atoll(ev) * 2000LL;
-  void* args[] = {&cc, &F, &NT, &G, &max_iter, &early_exit, &lm, &c2v, &lv, &lp, &xh, &zt, &active, &fail,
+  void* args[] = {&cc, &F, &NT, &G, &max_iter, &early_exit, &lm, &c2v, &lv, &lp, &yt, &ymag, &xh, &zt, &active, &fail,
                   &iters, &success, &synd_ok, &ctl, &bc};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(256), args, 0, s);
 }
 
 }  // namespace
-
-size_t resident_ctl_bytes() { return sizeof(ResidentCtl); }
-
-int resident_error(const void* ctl_host) { return static_cast<const ResidentCtl*>(ctl_host)->error; }
 
 // Tiles per group: as many as keep the group's messages, posteriors and
 // decisions within 3/4 of L2 (0 = one tile does not fit).
@@ -184,7 +188,7 @@ int resident_group(const DevCode& c, int n_tiles) {
     return 0;
   }
   const double per_tile = double(c.s_tot) * kLanes * sizeof(M) + 2.0 * c.n * kLanes * sizeof(M) +
-                          4.0 * (c.n + c.m_tot);
+                          4.0 * (2 * c.n + c.m_tot);
   int g = int(0.75 * l2 / per_tile);
   if (const char* ev = std::getenv("MBP_RESIDENT_GROUP_TILES")) g = std::atoi(ev);  // tuning override
   return g < 1 ? 0 : (g < n_tiles ? g : n_tiles);
@@ -208,12 +212,5 @@ cudaError_t launch_resident_any(const DevCode& c, const DevState& st, const Deco
     return launch_resident<M, 64>(c, st, a, G, l_max, s);
   }
 }
-
-template int resident_group<float>(const DevCode&, int);
-template int resident_group<double>(const DevCode&, int);
-template cudaError_t launch_resident_any<float>(const DevCode&, const DevState&, const DecodeArgs&, int, double,
-                                                cudaStream_t);
-template cudaError_t launch_resident_any<double>(const DevCode&, const DevState&, const DecodeArgs&, int, double,
-                                                 cudaStream_t);
 
 }  // namespace mbp

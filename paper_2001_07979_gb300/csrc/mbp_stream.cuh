@@ -27,32 +27,53 @@ using namespace dev;
 
 inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
-// One warp per (tile, check row): 8 rows per block, tile = blockIdx.y.
+// One warp per (tile, check row): 8 rows per block, tile = blockIdx.y, rows
+// p0 .. p1 - 1 (every row for flooding, one matrix's rows for the serial order).
 template <typename M, typename S, int DMAX, bool FIXED>
-__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int first_iter, S* __restrict__ c2v,
-                                                 const M* __restrict__ lsrc, const uint32_t* __restrict__ zt,
+__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int p0, int p1, int first_iter,
+                                                 S* __restrict__ c2v, const M* __restrict__ lsrc,
+                                                 const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
+                                                 const uint32_t* __restrict__ zt,
                                                  const uint32_t* __restrict__ active, M l_max,
                                                  int32_t* __restrict__ lacc, float qscale) {
   const int tile = blockIdx.y;
   const uint32_t act = active[tile];
   if (act == 0) return;
-  const int p = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (p >= c.m_tot) return;
-  cn_tile_row<M, S, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, zt, l_max, M(1) / l_max, lacc,
-                                          qscale);
+  const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= p1) return;
+  cn_tile_row<M, S, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, yt, ymag, zt, l_max,
+                                          M(1) / l_max, lacc, qscale);
+}
+
+// The min-sum check rule (variant), FP32 arithmetic; same layout as cn_kernel.
+template <typename S, int DMAX>
+__global__ void __launch_bounds__(256) cn_minsum_kernel(const DevCode c, int p0, int p1, int first_iter,
+                                                        S* __restrict__ c2v, const float* __restrict__ lsrc,
+                                                        const uint32_t* __restrict__ yt,
+                                                        const float* __restrict__ ymag,
+                                                        const uint32_t* __restrict__ zt,
+                                                        const uint32_t* __restrict__ active, float l_max) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= p1) return;
+  const CnView<float, S> v = cn_view<float, S, kPolStream>(c, tile, act, first_iter, c2v, lsrc, yt, ymag, zt, nullptr);
+  cn_view_row_minsum<S, DMAX, kPolStream>(v, p, first_iter, l_max);
 }
 
 // One warp per (tile, variable node): 8 nodes per block.
 template <typename M, typename S>
 __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __restrict__ c2v, M* __restrict__ lv,
-                                                 const M* __restrict__ lp, uint32_t* __restrict__ xh,
+                                                 const M* __restrict__ lp, const uint32_t* __restrict__ yt,
+                                                 const M* __restrict__ ymag, uint32_t* __restrict__ xh,
                                                  const uint32_t* __restrict__ active) {
   const int tile = blockIdx.y;
   const uint32_t act = active[tile];
   if (act == 0) return;
   const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= c.n) return;
-  vn_node<M, S, kPolStream>(c, tile, col, act, c2v, lv, lp, xh);
+  vn_node<M, S, kPolStream>(c, tile, col, act, c2v, lv, lp, yt, ymag, xh);
 }
 
 // L_V = L_P + lacc / qscale and the hard decision, for the fixed-point single
@@ -60,6 +81,7 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __res
 template <typename M>
 __global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const int32_t* __restrict__ lacc,
                                                        M* __restrict__ lv, const M* __restrict__ lp,
+                                                       const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                                        uint32_t* __restrict__ xh, const uint32_t* __restrict__ active,
                                                        float inv_qscale) {
   const int tile = blockIdx.y;
@@ -68,8 +90,9 @@ __global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const in
   const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= c.n) return;
   const int lane = threadIdx.x & 31;
-  const int64_t at = (int64_t(tile) * c.n + col) * kLanes + lane;
-  const M sum = lp[at] + M(float(lacc[at]) * inv_qscale);
+  const int64_t tn = int64_t(tile) * c.n + col;
+  const int64_t at = tn * kLanes + lane;
+  const M sum = channel_llr<M, kPolStream>(lp, yt, ymag, tn, tile, lane) + M(float(lacc[at]) * inv_qscale);
   if ((act >> lane) & 1u) lv[at] = sum;
   const uint32_t hard = __ballot_sync(kFull, sum < M(0));
   if (lane == 0) {
@@ -100,20 +123,39 @@ __global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, in
     atomicAdd(&counters[0], 1);
 }
 
+// Rows p0 .. p1 - 1 of every tile that is still decoding, from the posterior (or L_P) lsrc, or from the sign
+// words yt in the first iteration of BSC inputs.
+struct CnLaunch {
+  int p0, p1, first_iter;
+  const void* lsrc;
+  const uint32_t* yt;
+};
+
 template <typename M, typename S, int DMAX, bool FIXED>
-void launch_cn(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale, cudaStream_t s) {
-  const dim3 grid(blocks_for(c.m_tot, 8), st.n_tiles);
-  cn_kernel<M, S, DMAX, FIXED><<<grid, 256, 0, s>>>(c, first_iter, static_cast<S*>(st.c2v),
-                                                 static_cast<const M*>(first_iter ? st.lp : st.lv), st.zt, st.active,
-                                                 M(l_max), st.lacc, qscale);
+void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l_max, float qscale, int rule,
+               cudaStream_t s) {
+  const dim3 grid(blocks_for(q.p1 - q.p0, 8), st.n_tiles);
+  if constexpr (sizeof(M) == 4 && !FIXED) {
+    if (rule == MBP_RULE_MIN_SUM) {
+      cn_minsum_kernel<S, DMAX><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
+                                                     static_cast<const float*>(q.lsrc), q.yt,
+                                                     static_cast<const float*>(st.chan_mag), st.zt, st.active,
+                                                     float(l_max));
+      return;
+    }
+  }
+  cn_kernel<M, S, DMAX, FIXED><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
+                                                 static_cast<const M*>(q.lsrc), q.yt,
+                                                 static_cast<const M*>(st.chan_mag), st.zt, st.active, M(l_max),
+                                                 st.lacc, qscale);
 }
 
 // Unroll bound at or one above the largest check degree (the last two degrees run without per-edge tests).
 template <typename M, typename S, bool FIXED>
-void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double l_max, float qscale,
+void launch_cn_any(const DevCode& c, const DevState& st, const CnLaunch& q, double l_max, float qscale, int rule,
                    cudaStream_t s) {
   const int d = c.max_row_deg;
-#define MBP_CN(D) launch_cn<M, S, D, FIXED>(c, st, first_iter, l_max, qscale, s)
+#define MBP_CN(D) launch_cn<M, S, D, FIXED>(c, st, q, l_max, qscale, rule, s)
   if constexpr (sizeof(M) == 4 && !FIXED) {
     if (d <= 4) MBP_CN(4);
     else if (d <= 6) MBP_CN(6);
@@ -135,6 +177,36 @@ void launch_cn_any(const DevCode& c, const DevState& st, int first_iter, double 
     else MBP_CN(64);
   }
 #undef MBP_CN
+}
+
+// One flooding sum-product iteration of one group without any host synchronisation (the grid kernels of the
+// grouped decode): eq. (6) over every row, eq. (2) and the hard decision, and the stopping test; the caller
+// retires the finished frames.
+template <typename M, typename S>
+cudaError_t group_step(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s) {
+  const int NT = st.n_tiles;
+  const CnLaunch q{0, c.m_tot, first_iter, first_iter ? st.lp : st.lv, st.yt};
+  prof_begin(MBP_KERNEL_CHECK, s);
+  launch_cn_any<M, S, false>(c, st, q, l_max, 0.f, MBP_RULE_SUM_PRODUCT, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  prof_end(MBP_KERNEL_CHECK, s, 1);
+  prof_begin(MBP_KERNEL_VARIABLE, s);
+  vn_kernel<M, S><<<dim3(blocks_for(c.n, 8), NT), 256, 0, s>>>(c, static_cast<const S*>(st.c2v),
+                                                                 static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
+                                                                 st.yt, static_cast<const M*>(st.chan_mag), st.xh,
+                                                                 st.active);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  prof_end(MBP_KERNEL_VARIABLE, s, 1);
+  prof_begin(MBP_KERNEL_SYNDROME, s);
+  const dim3 syn_grid(blocks_for(c.m_tot, 256), NT);
+  if (c.max_row_deg <= 8) syn_kernel<8><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+  else if (c.max_row_deg <= 16) syn_kernel<16><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+  else if (c.max_row_deg <= 32) syn_kernel<32><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+  else syn_kernel<kMaxRowDeg><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  prof_end(MBP_KERNEL_SYNDROME, s, 1);
+  return cudaSuccess;
 }
 
 template <typename M, typename S>
@@ -172,25 +244,49 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
   if (a.early_exit || a.max_iter == 0) {
     if ((rc = stop_check(0, &left))) return rc;
   }
-  for (int t = 1; t <= a.max_iter && left > 0; ++t) {
-    prof_begin(MBP_KERNEL_CHECK, s);
-    if constexpr (sizeof(M) == 4 && sizeof(S) == 4) {
-      if (fixed) launch_cn_any<M, S, true>(c, st, t == 1, l_max, qscale, s);
-      else launch_cn_any<M, S, false>(c, st, t == 1, l_max, qscale, s);
-    } else {
-      launch_cn_any<M, S, false>(c, st, t == 1, l_max, qscale, s);
-    }
-    CKL("cn_kernel");
-    prof_end(MBP_KERNEL_CHECK, s, 1);
+  auto variable = [&]() -> int {
     prof_begin(MBP_KERNEL_VARIABLE, s);
     if (fixed)
       finalize_kernel<M><<<node_grid, 256, 0, s>>>(c, st.lacc, static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
-                                                   st.xh, st.active, inv_qscale);
+                                                   st.yt, static_cast<const M*>(st.chan_mag), st.xh, st.active,
+                                                   inv_qscale);
     else
       vn_kernel<M, S><<<node_grid, 256, 0, s>>>(c, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv),
-                                             static_cast<const M*>(st.lp), st.xh, st.active);
+                                             static_cast<const M*>(st.lp), st.yt,
+                                             static_cast<const M*>(st.chan_mag), st.xh, st.active);
     CKL("vn_kernel");
     prof_end(MBP_KERNEL_VARIABLE, s, 1);
+    return MBP_OK;
+  };
+  auto check = [&](const CnLaunch& q) -> int {
+    prof_begin(MBP_KERNEL_CHECK, s);
+    if constexpr (sizeof(M) == 4 && sizeof(S) == 4) {
+      if (fixed) launch_cn_any<M, S, true>(c, st, q, l_max, qscale, a.rule, s);
+      else launch_cn_any<M, S, false>(c, st, q, l_max, qscale, a.rule, s);
+    } else {
+      launch_cn_any<M, S, false>(c, st, q, l_max, qscale, a.rule, s);
+    }
+    CKL("cn_kernel");
+    prof_end(MBP_KERNEL_CHECK, s, 1);
+    return MBP_OK;
+  };
+  const bool serial = a.update == MBP_UPDATE_MATRIX_SERIAL && c.u > 1;
+  if (serial && a.max_iter > 0 && left > 0)  // matrices not yet visited in iteration 1 contribute 0 to eq. (2)
+    CK(cudaMemsetAsync(st.c2v, 0, size_t(NT) * c.s_tot * kLanes * sizeof(S), s), "clear messages");
+  for (int t = 1; t <= a.max_iter && left > 0; ++t) {
+    if (serial) {
+      // Algorithm 1's nesting: each matrix's checks, then eq. (2) with its new messages, before the next matrix
+      for (int l = 0; l < c.u; ++l) {
+        const bool from_lp = t == 1 && l == 0;
+        const CnLaunch q{c.row_pos[l], c.row_pos[l + 1], t == 1, from_lp ? st.lp : st.lv, from_lp ? st.yt : nullptr};
+        if ((rc = check(q))) return rc;
+        if ((rc = variable())) return rc;
+      }
+    } else {
+      const CnLaunch q{0, c.m_tot, t == 1, t == 1 ? st.lp : st.lv, st.yt};
+      if ((rc = check(q))) return rc;
+      if ((rc = variable())) return rc;
+    }
     if (a.early_exit || t == a.max_iter) {
       if ((rc = stop_check(t, &left))) return rc;
     }

@@ -9,4 +9,10 @@ int stream_iterations<float, __half>(const DevCode& c, DevState& st, const Decod
   return stream::run<float, __half>(c, st, a, fixed, l_max, qscale, inv_qscale, s);
 }
 
+template <>
+cudaError_t stream_group_step<float, __half>(const DevCode& c, const DevState& st, int first_iter, double l_max,
+                                         cudaStream_t s) {
+  return stream::group_step<float, __half>(c, st, first_iter, l_max, s);
+}
+
 }  // namespace mbp

@@ -100,7 +100,7 @@ def test_bsc_llr_matches_oracle(mbp):
 
 # ------------------------------------------------------- whole decoder
 
-MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident", "f16", "bf16"]
+MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident", "f16", "bf16", "f32-graph", "f16-graph"]
 
 
 def mode_args(mbp, mode):
@@ -116,6 +116,10 @@ def mode_args(mbp, mode):
         return dict(msg_dtype=mbp.MSG_F16)
     if mode == "bf16":
         return dict(msg_dtype=mbp.MSG_BF16)
+    if mode == "f32-graph":
+        return dict(msg_dtype=mbp.MSG_F32, schedule=mbp.SCHED_GRAPH)
+    if mode == "f16-graph":
+        return dict(msg_dtype=mbp.MSG_F16, schedule=mbp.SCHED_GRAPH)
     return dict(msg_dtype=mbp.MSG_F32, schedule=mbp.SCHED_RESIDENT)
 
 
@@ -123,6 +127,7 @@ def mode_args(mbp, mode):
 # l_max = 20, in natural-log units): the L_V of a node with d edges can differ from FP32 by d times that after
 # the first iteration. Later iterations carry these differences on; their size is reported, not bounded.
 STORE_ROUNDOFF = {"f16": 2.0 ** -11 * 32.0 * 0.6931471805599453, "bf16": 2.0 ** -8 * 32.0 * 0.6931471805599453}
+STORE_ROUNDOFF["f16-graph"] = STORE_ROUNDOFF["f16"]
 
 
 def tolerance(mode, t, max_col_deg):
@@ -170,9 +175,10 @@ def test_messages_within_tolerance_first_iterations(mbp, mode, t):
     tol = tolerance(mode, t, codes_max_col_deg(w.H))
     ref_c2v = orc.decode(w.H, orc.bsc_llr(w.y, w.n, w.e), w.z_orc, t, early_exit=False, want_c2v=True)["c2v"]
     err_lv = np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"]))
-    dt = mode_args(mbp, mode)["msg_dtype"]
-    err_c2v = max(np.max(np.abs(mbp.mbp_export_c2v(codes, w.F, out["workspace"], f, dt).cpu().numpy() - ref_c2v[f]))
-                  for f in range(w.F))
+    kw = mode_args(mbp, mode)
+    dt, sched = kw["msg_dtype"], kw.get("schedule", mbp.SCHED_AUTO)
+    err_c2v = max(np.max(np.abs(mbp.mbp_export_c2v(codes, w.F, out["workspace"], f, dt, schedule=sched).cpu().numpy()
+                                - ref_c2v[f])) for f in range(w.F))
     print(f"{mode} t={t}: max |dL_V| = {err_lv:.3g}, max |dC2V| = {err_c2v:.3g}")
     if tol is not None:
         assert err_lv <= tol and err_c2v <= tol
@@ -202,7 +208,7 @@ def codes_max_col_deg(H):
     return int(np.max(sum(h.col_degrees() for h in H)))
 
 
-@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed", "f32-resident", "f16", "bf16"])
+@pytest.mark.parametrize("mode", ["f32-float", "f32-fixed", "f32-resident", "f16", "bf16", "f32-graph"])
 def test_rate07_n65536_subset_bit_exact(mbp, mode):
     """n=65536, R=0.7, d_v {2,3,8}, u=2, QBER 2%: 64 frames, max 60 iterations."""
     w = Workload(65536, 19661, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 1, 64, 0.02)
@@ -397,17 +403,18 @@ def test_accumulation_modes_agree(mbp):
 
 @pytest.mark.parametrize("early_exit", [True, False])
 def test_schedules_agree_bit_for_bit(mbp, early_exit):
-    """The streaming and resident schedules run the same arithmetic in the same order."""
+    """The streaming, resident and graph schedules run the same arithmetic in the same order."""
     w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 3, 7, 45, 0.06)
     codes = mbp.mbp_create_codes(w.H)
     z = gpu_syndrome(mbp, codes, w.x)
     y, e = dev(u32_to_i32(w.y)), dev(w.e)
     a = mbp.mbp_decode_bsc(codes, y, e, z, 25, early_exit=early_exit, want_soft=True, want_synd=True,
                            schedule=mbp.SCHED_STREAMING)
-    b = mbp.mbp_decode_bsc(codes, y, e, z, 25, early_exit=early_exit, want_soft=True, want_synd=True,
-                           schedule=mbp.SCHED_RESIDENT)
-    for k in ("x_hat_bits", "iters", "success", "synd_ok", "soft"):
-        assert torch.equal(a[k], b[k]), k
+    for sched in (mbp.SCHED_RESIDENT, mbp.SCHED_GRAPH):
+        b = mbp.mbp_decode_bsc(codes, y, e, z, 25, early_exit=early_exit, want_soft=True, want_synd=True,
+                               schedule=sched)
+        for k in ("x_hat_bits", "iters", "success", "synd_ok", "soft"):
+            assert torch.equal(a[k], b[k]), (sched, k)
 
 
 def test_resident_barrier_timeout_reports_etimeout(mbp, monkeypatch):
