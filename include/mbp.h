@@ -321,6 +321,13 @@ typedef struct {
 int mbp_autotune_multi(const mbp_group* groups, int G, int max_iter, const mbp_opts* opts, mbp_tuning* best,
                        mbp_stream_t stream);
 
+/*
+ * Set the launch shape that later mbp_decode_multi calls use for these codes and frame counts on the current
+ * device and message type (as mbp_autotune_multi leaves it), e.g. one found by an earlier autotuning run.
+ * cn_warps, vn_warps and syn_warps in {2, 4, 8}; cn_waves in {1, 2}; ms is ignored.
+ */
+int mbp_multi_set_tuning(const mbp_group* groups, int G, const mbp_opts* opts, const mbp_tuning* tuning);
+
 /* Drop the library's cached graphs and tuned shapes (for example before freeing a workspace that a cached graph
  * refers to and allocating another at the same address; a graph never reads a workspace outside a decode call). */
 int mbp_release_cached(void);

@@ -31,6 +31,7 @@ __all__ = [
     "mbp_decode_batch", "mbp_decode_bsc", "mbp_decode_bsc_host", "mbp_export_c2v", "mbp_version",
     "split_syndromes", "join_syndromes", "mbp_profile_enable", "mbp_profile_get", "KERNEL_FAMILIES",
     "mbp_multi_workspace_size", "mbp_decode_multi", "mbp_autotune_multi", "mbp_release_cached",
+    "mbp_multi_set_tuning",
     "mbp_nbp_workspace_size", "mbp_nbp_forward", "mbp_nbp_backward", "NormalizedBP", "NBPDecoder",
 ]
 
@@ -108,6 +109,7 @@ def _load():
             "mbp_decode_multi": (I, [P, I, I, P, P]),
             "mbp_autotune_multi": (I, [P, I, I, P, P, P]),
             "mbp_release_cached": (I, []),
+            "mbp_multi_set_tuning": (I, [P, I, P, P]),
             "mbp_nbp_workspace_size": (I, [P, I, I, P]),
             "mbp_nbp_forward": (I, [P, I, I, P, P, P, P, ctypes.c_double, P, S, P, P]),
             "mbp_nbp_backward": (I, [P, I, I, P, P, ctypes.c_double, P, P, S, P, P, P, P]),
@@ -443,6 +445,16 @@ def mbp_autotune_multi(groups, max_iter: int, *, msg_dtype: int = MSG_F32, l_max
                   workspace, stream, extra=(ctypes.byref(best),))
     return outs, dict(grid_kernels=best.grid_kernels, cn_warps=best.cn_warps, cn_waves=best.cn_waves, vn_warps=best.vn_warps,
                       syn_warps=best.syn_warps, ms=best.ms)
+
+
+def mbp_multi_set_tuning(groups, tuning: dict, msg_dtype: int = MSG_F32):
+    """Use this launch shape ({grid_kernels, cn_warps, cn_waves, vn_warps, syn_warps}) for later
+    mbp_decode_multi calls on these codes and frame counts."""
+    arr, _, _ = _groups(groups, False, False, alloc=False)
+    o = _opts(msg_dtype, 20.0, True, False, False)
+    t = _Tuning(int(tuning.get("grid_kernels", 1)), int(tuning.get("cn_warps", 8)), int(tuning.get("cn_waves", 1)),
+                int(tuning.get("vn_warps", 8)), int(tuning.get("syn_warps", 8)), 0.0)
+    _check(_load().mbp_multi_set_tuning(arr, len(groups), ctypes.byref(o), ctypes.byref(t)))
 
 
 def mbp_release_cached():

@@ -329,6 +329,31 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
     std::vector<int32_t> fill(col_ptr.begin(), col_ptr.end() - 1);
     for (int64_t e = 0; e < e_tot; ++e) col_slot[fill[col_idx[e]]++] = edge_slot[e];  // stacked-row order
   }
+  // variable nodes by degree class, each with a dense table of its slots (the variable-node kernel then
+  // loads a node and its slots together)
+  std::vector<int32_t> vnode(n), vslot(std::max<int64_t>(e_tot, 1));
+  for (int32_t i = 0; i < n; ++i) vnode[i] = i;
+  std::stable_sort(vnode.begin(), vnode.end(), [&](int32_t a, int32_t b) {
+    return col_ptr[a + 1] - col_ptr[a] < col_ptr[b + 1] - col_ptr[b];
+  });
+  d.n_vclass = 0;
+  {
+    int64_t t = 0;
+    bool fits = true;
+    for (int32_t q = 0; q < n; ++q) {
+      const int32_t i = vnode[q], deg = col_ptr[i + 1] - col_ptr[i];
+      if (q == 0 || deg != d.vclass_deg[d.n_vclass - 1]) {
+        if (d.n_vclass == kMaxVClasses) { fits = false; break; }
+        d.vclass_deg[d.n_vclass] = deg;
+        d.vclass_first[d.n_vclass] = q;
+        d.vclass_toff[d.n_vclass] = t;
+        ++d.n_vclass;
+      }
+      for (int32_t a = col_ptr[i]; a < col_ptr[i + 1]; ++a) vslot[t++] = col_slot[a];
+    }
+    if (fits) d.vclass_first[d.n_vclass] = n;
+    else d.n_vclass = 0;
+  }
 
   // ---- one device block for every array
   struct Part { const void* src; size_t bytes; size_t off; };
@@ -337,7 +362,8 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
       {col_ptr.data(), col_ptr.size() * 4, 0},       {col_slot.data(), col_slot.size() * 4, 0},
       {row_ptr.data(), row_ptr.size() * 4, 0},       {col_idx.data(), col_idx.size() * 4, 0},
       {edge_slot.data(), edge_slot.size() * 4, 0},   {perm_mat.data(), perm_mat.size(), 0},
-      {perm_local.data(), perm_local.size() * 4, 0}};
+      {perm_local.data(), perm_local.size() * 4, 0}, {vnode.data(), vnode.size() * 4, 0},
+      {vslot.data(), vslot.size() * 4, 0}};
   size_t total = 0;
   for (auto& p : parts) {
     p.off = total;
@@ -372,6 +398,8 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   d.edge_slot = reinterpret_cast<const int32_t*>(base + parts[6].off);
   d.row_mat = reinterpret_cast<const uint8_t*>(base + parts[7].off);
   d.row_local = reinterpret_cast<const int32_t*>(base + parts[8].off);
+  d.vnode = reinterpret_cast<const int32_t*>(base + parts[9].off);
+  d.vslot = reinterpret_cast<const int32_t*>(base + parts[10].off);
   h->d = d;
   *out = h;
   return MBP_OK;
@@ -694,6 +722,18 @@ int mbp_autotune_multi(const mbp_group* groups, int G, int max_iter, const mbp_o
   int rc = check_groups(groups, G, opts, true);
   if (rc) return rc;
   return multi_autotune(groups, G, max_iter, opts, best, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mbp_multi_set_tuning(const mbp_group* groups, int G, const mbp_opts* opts, const mbp_tuning* tuning) {
+  g_err.clear();
+  REQUIRE(tuning, "tuning is NULL");
+  int rc = check_groups(groups, G, opts, false);
+  if (rc) return rc;
+  auto ok = [](int w) { return w == 2 || w == 4 || w == 8; };
+  REQUIRE(ok(tuning->cn_warps) && ok(tuning->vn_warps) && ok(tuning->syn_warps) &&
+              (tuning->cn_waves == 1 || tuning->cn_waves == 2),
+          "tuning: warps per block must be 2, 4 or 8 and cn_waves 1 or 2");
+  return multi_set_tuning(groups, G, opts, tuning);
 }
 
 int mbp_release_cached(void) {

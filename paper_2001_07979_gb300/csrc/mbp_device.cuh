@@ -199,7 +199,8 @@ __device__ __forceinline__ M channel_llr(const M* __restrict__ lp, const uint32_
 //
 // ysrc != NULL: the first iteration of BSC inputs, where V2C = L_P comes from
 // the sign words ysrc (bit = lane) and this lane's magnitude ymag instead of
-// gsrc (a warp-uniform branch at the loads; the arithmetic is shared).
+// gsrc (a warp-uniform branch): all of the frame's V2C then share one
+// magnitude, and the row's output magnitude is formed once.
 //
 // FIXED: also add each edge's change of message, q(C2V_new) - q(C2V_old) with
 // q(x) = round(x * qscale), to the posterior accumulator lacc of its variable
@@ -216,10 +217,34 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : -1;
   M v[D];
   if (ysrc) {
+    // First iteration of BSC inputs: every V2C of this frame has the magnitude ymag, so the row's
+    // combination of the other edges is the same deg - 1 fold for every edge: delta, D and the output
+    // magnitude are formed once per row, and each edge only takes its sign.
     const int lane = threadIdx.x & 31;
+    uint32_t sgn[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      sgn[k] = (!CHECKED || col[k] >= 0) ? ((ld_state<POL>(ysrc + col[k]) >> lane) & 1u) << 31 : 0u;
+      par ^= sgn[k];
+    }
+    if (!store) return;
+    const M d = Arith<M>::delta(Arith<M>::clip_abs(ymag, l_max, inv_l_max));
+    M P = M(0);
+#pragma unroll
+    for (int k = 0; k < D - 1; ++k)
+      if (!CHECKED || k + 1 < deg) P = Arith<M>::oplus(P, d);
+    const M mag = Arith<M>::clipped_mag(P, l_max, inv_l_max);
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      v[k] = (!CHECKED || col[k] >= 0) ? (((ld_state<POL>(ysrc + col[k]) >> lane) & 1u) ? -ymag : ymag) : M(0);
+      if (!CHECKED || col[k] >= 0) {
+        const M nv = Bits<M>::copy_sign(mag, par ^ sgn[k]);
+        st_msg<POL>(msg + k * kLanes, Store<S>::narrow(nv));
+        if constexpr (FIXED) {
+          const int32_t dq = __float2int_rn(float(nv) * qscale);
+          if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
+        }
+      }
+    return;
   } else {
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : M(0);
@@ -473,12 +498,10 @@ __device__ __forceinline__ VnView<M, S> vn_view(const DevCode& c, int tile, uint
 // soft decision L_V = L_P + sum of the node's C2V over all matrices (eq. 2) and
 // the hard decision, whose 32 lanes are one word of xh. Nodes with more than 16
 // edges are summed 16 edges at a time, still in stacked-row order.
+// The update of node `col` of the view's tile from its d slots (in stacked-row order).
 template <typename M, typename S, int POL>
-__device__ __forceinline__ void vn_view_node(const VnView<M, S>& v, int col) {
+__device__ __forceinline__ void vn_core(const VnView<M, S>& v, int col, const int32_t* __restrict__ slots, int d) {
   const int lane = threadIdx.x & 31;
-  const int a0 = v.col_ptr[col];
-  const int d = v.col_ptr[col + 1] - a0;
-  const int* slots = v.col_slot + a0;
   M sum;
   if (v.yt) sum = ((ld_state<POL>(v.yt + col) >> lane) & 1u) ? -v.ym : v.ym;
   else sum = ld_state<POL>(v.lp + int64_t(col) * kLanes);
@@ -488,11 +511,20 @@ __device__ __forceinline__ void vn_view_node(const VnView<M, S>& v, int col) {
     for (int b = 0; b < d; b += 16) sum = vn_sum<M, S, 16, POL>(slots + b, d - b, v.msg, sum);
   if ((v.act >> lane) & 1u) v.lv[int64_t(col) * kLanes] = sum;
   const uint32_t hard = __ballot_sync(kFull, sum < M(0));
-  if (lane == 0) {
+  if (lane == 0) {  // retired lanes keep their decision
     uint32_t* px = v.xh + col;
-    const uint32_t prev = ld_state<POL>(px);
-    *px = (prev & ~v.act) | (hard & v.act);
+    *px = v.act == kFull ? hard : (ld_state<POL>(px) & ~v.act) | (hard & v.act);
   }
+}
+
+// The variable-node update of node `col` of the view's tile, by one warp: the
+// soft decision L_V = L_P + sum of the node's C2V over all matrices (eq. 2) and
+// the hard decision, whose 32 lanes are one word of xh. Nodes with more than 16
+// edges are summed 16 edges at a time, still in stacked-row order.
+template <typename M, typename S, int POL>
+__device__ __forceinline__ void vn_view_node(const VnView<M, S>& v, int col) {
+  const int a0 = v.col_ptr[col];
+  vn_core<M, S, POL>(v, col, v.col_slot + a0, v.col_ptr[col + 1] - a0);
 }
 
 template <typename M, typename S, int POL>

@@ -31,6 +31,7 @@ constexpr int kMaxU = 16;
 constexpr int kMaxRowDeg = 64;
 constexpr int kMaxDevices = 64;
 constexpr int kMaxColDeg = 64;  // a variable node's edges over all u matrices
+constexpr int kMaxVClasses = 8;  // variable-node degree classes with slot tables of their own
 constexpr int kMaxQBits = 24;   // fixed-point accumulation: at most 2^-24 resolution
 constexpr int kMinQBits = 12;   // and at least 2^-12
 
@@ -51,6 +52,16 @@ struct DevCode {
   const int32_t* edge_slot;   // [e_tot] stacked CSR edge -> slot
   const uint8_t* row_mat;     // [m_tot] matrix l of the row at position p
   const int32_t* row_local;   // [m_tot] row index j inside H_l of the row at position p
+  // Variable nodes grouped by their degree over all matrices (n_vclass = 0 when there are more classes than
+  // kMaxVClasses): class k holds node positions vclass_first[k] .. vclass_first[k+1] - 1, all of degree
+  // vclass_deg[k]; vnode gives the node at each position, and the class's slots (col_slot order, one row of
+  // vclass_deg[k] per position) start at vslot + vclass_toff[k].
+  int32_t n_vclass;
+  int32_t vclass_deg[kMaxVClasses];
+  int32_t vclass_first[kMaxVClasses + 1];
+  int64_t vclass_toff[kMaxVClasses];
+  const int32_t* vnode;       // [n]
+  const int32_t* vslot;       // [e_tot]
 };
 
 // Per-call decoder state carved out of the caller's workspace.

@@ -548,6 +548,15 @@ int multi_autotune(const mbp_group* g, int G, int max_iter, const mbp_opts* o, m
   return run_multi(g, G, max_iter, o, false, &best, s);
 }
 
+int multi_set_tuning(const mbp_group* g, int G, const mbp_opts* o, const mbp_tuning* t) {
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  MultiTuning tu{t->grid_kernels ? 1 : 0, t->cn_warps, t->cn_waves, t->vn_warps, t->syn_warps};
+  remember_tuning(device, o->msg_dtype, g, G, tu);
+  return MBP_OK;
+}
+
 void multi_release() {
   std::lock_guard<std::mutex> lock(g_mu);
   for (auto& ge : g_graphs) cudaGraphExecDestroy(ge.exec);

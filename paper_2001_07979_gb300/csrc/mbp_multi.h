@@ -106,6 +106,7 @@ int multi_workspace(const mbp_group* g, int G, const mbp_opts* o, bool host_io, 
 int multi_group_state(const mbp_group* g, int G, int index, const mbp_opts* o, bool host_io, DevState* st);
 int multi_decode(const mbp_group* g, int G, int max_iter, const mbp_opts* o, bool host_io, cudaStream_t s);
 int multi_autotune(const mbp_group* g, int G, int max_iter, const mbp_opts* o, mbp_tuning* best, cudaStream_t s);
+int multi_set_tuning(const mbp_group* g, int G, const mbp_opts* o, const mbp_tuning* t);
 void multi_release();
 
 }  // namespace mbp

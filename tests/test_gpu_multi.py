@@ -263,3 +263,19 @@ def test_uneven_batch_recipe_small(mbp):
         ok += int(s.sum())
         assert np.array_equal(o["x_hat_bits"].cpu().numpy().view(np.uint32)[s], x[s])
     assert ok >= 200
+
+
+def test_set_tuning_selects_kernels_without_changing_results(mbp, batch):
+    ref = mbp.mbp_decode_multi([g.arg() for g in batch], 30, want_soft=True)
+    torch.cuda.synchronize()
+    for tu in (dict(grid_kernels=0, cn_warps=2, cn_waves=2, vn_warps=4, syn_warps=8),
+               dict(grid_kernels=1, cn_warps=8, cn_waves=1, vn_warps=8, syn_warps=8)):
+        mbp.mbp_multi_set_tuning([g.arg() for g in batch], tu)
+        out = mbp.mbp_decode_multi([g.arg() for g in batch], 30, want_soft=True)
+        torch.cuda.synchronize()
+        for a, b in zip(ref, out):
+            for k in ("x_hat_bits", "iters", "success", "soft"):
+                assert torch.equal(a[k], b[k]), (tu, k)
+    with pytest.raises(mbp.MBPError) as ei:
+        mbp.mbp_multi_set_tuning([g.arg() for g in batch], dict(cn_warps=16))
+    assert ei.value.status == 1
