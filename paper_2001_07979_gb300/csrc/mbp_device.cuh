@@ -207,6 +207,41 @@ __device__ __forceinline__ M channel_llr(const M* __restrict__ lp, const uint32_
 // node (a 32-bit red.global.add in L2). Integer addition is associative, so
 // the accumulated sum sum_e q(C2V_e) is exact and independent of the order of
 // the atomics; finalize_kernel turns it into L_V.
+// First iteration of BSC inputs: every V2C of a frame has the magnitude ymag,
+// so the combination of a row's other edges is the same deg - 1 fold for every
+// edge; its output magnitude is formed once per row.
+template <typename M, int D, bool CHECKED>
+__device__ __forceinline__ M cn_first_mag(int deg, M ymag, M l_max, M inv_l_max) {
+  const M d = Arith<M>::delta(Arith<M>::clip_abs(ymag, l_max, inv_l_max));
+  M P = M(0);
+#pragma unroll
+  for (int k = 0; k < D - 1; ++k)
+    if (!CHECKED || k + 1 < deg) P = Arith<M>::oplus(P, d);
+  return Arith<M>::clipped_mag(P, l_max, inv_l_max);
+}
+
+// The first-iteration row of BSC inputs (see cn_first_mag): each edge takes the
+// shared magnitude with the sign of the other edges' bits and z_j. The row's
+// bits are kept as one mask (D <= 32), edges k >= deg are padding.
+template <typename M, typename S, int D, bool CHECKED, int POL>
+__device__ __forceinline__ void cn_row_signs(int deg, const int* __restrict__ cols, const uint32_t* __restrict__ ysrc,
+                                             M ymag, S* __restrict__ msg, uint32_t par, bool store, M l_max,
+                                             M inv_l_max) {
+  static_assert(D <= 32, "one bit per edge");
+  const int lane = threadIdx.x & 31;
+  uint32_t bits = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (!CHECKED || k < deg) bits |= ((ld_state<POL>(ysrc + __ldg(cols + k)) >> lane) & 1u) << k;
+  if (!store) return;
+  par ^= uint32_t(__popc(bits) & 1) << 31;
+  const M mag = cn_first_mag<M, D, CHECKED>(deg, ymag, l_max, inv_l_max);
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (!CHECKED || k < deg)
+      st_msg<POL>(msg + k * kLanes, Store<S>::narrow(Bits<M>::copy_sign(mag, par ^ (((bits >> k) & 1u) << 31))));
+}
+
 template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL>
 __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, const M* __restrict__ gsrc,
                                        const uint32_t* __restrict__ ysrc, M ymag, S* __restrict__ msg,
@@ -217,34 +252,31 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : -1;
   M v[D];
   if (ysrc) {
-    // First iteration of BSC inputs: every V2C of this frame has the magnitude ymag, so the row's
-    // combination of the other edges is the same deg - 1 fold for every edge: delta, D and the output
-    // magnitude are formed once per row, and each edge only takes its sign.
-    const int lane = threadIdx.x & 31;
-    uint32_t sgn[D];
+    if constexpr (!FIXED && D <= 32) {
+      cn_row_signs<M, S, D, CHECKED, POL>(deg, cols, ysrc, ymag, msg, par, store, l_max, inv_l_max);
+      return;
+    } else {
+      const int lane = threadIdx.x & 31;
+      uint32_t sgn[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      sgn[k] = (!CHECKED || col[k] >= 0) ? ((ld_state<POL>(ysrc + col[k]) >> lane) & 1u) << 31 : 0u;
-      par ^= sgn[k];
-    }
-    if (!store) return;
-    const M d = Arith<M>::delta(Arith<M>::clip_abs(ymag, l_max, inv_l_max));
-    M P = M(0);
-#pragma unroll
-    for (int k = 0; k < D - 1; ++k)
-      if (!CHECKED || k + 1 < deg) P = Arith<M>::oplus(P, d);
-    const M mag = Arith<M>::clipped_mag(P, l_max, inv_l_max);
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-      if (!CHECKED || col[k] >= 0) {
-        const M nv = Bits<M>::copy_sign(mag, par ^ sgn[k]);
-        st_msg<POL>(msg + k * kLanes, Store<S>::narrow(nv));
-        if constexpr (FIXED) {
-          const int32_t dq = __float2int_rn(float(nv) * qscale);
-          if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
-        }
+      for (int k = 0; k < D; ++k) {
+        sgn[k] = (!CHECKED || col[k] >= 0) ? ((ld_state<POL>(ysrc + col[k]) >> lane) & 1u) << 31 : 0u;
+        par ^= sgn[k];
       }
-    return;
+      if (!store) return;
+      const M mag = cn_first_mag<M, D, CHECKED>(deg, ymag, l_max, inv_l_max);
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        if (!CHECKED || col[k] >= 0) {
+          const M nv = Bits<M>::copy_sign(mag, par ^ sgn[k]);
+          st_msg<POL>(msg + k * kLanes, Store<S>::narrow(nv));
+          if constexpr (FIXED) {
+            const int32_t dq = __float2int_rn(float(nv) * qscale);
+            if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
+          }
+        }
+      return;
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : M(0);
@@ -492,6 +524,43 @@ __device__ __forceinline__ VnView<M, S> vn_view(const DevCode& c, int tile, uint
   v.xh = xh + int64_t(tile) * c.n;
   v.act = act;
   return v;
+}
+
+// The update of N nodes of one degree class (degree d <= D) by one warp, all of
+// their gathers in flight together: node j is vnode[q0 + j] with slots at
+// slots0 + j * d (j < cnt). Each node's sum runs in the order of vn_core.
+template <typename M, typename S, int D, int N, int POL>
+__device__ __forceinline__ void vn_class_nodes(const VnView<M, S>& v, const int32_t* __restrict__ vnode, int q0,
+                                               const int32_t* __restrict__ slots0, int d, int cnt) {
+  const int lane = threadIdx.x & 31;
+  int col[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) col[j] = j < cnt ? __ldg(vnode + q0 + j) : -1;
+  M g[N][D];
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const bool on = j < cnt && k < d;
+      const int slot = on ? __ldg(slots0 + j * d + k) : 0;
+      g[j][k] = on ? M(Store<S>::widen(ld_msg<POL>(v.msg + int64_t(slot) * kLanes))) : M(0);
+    }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j >= cnt) break;
+    M sum;
+    if (v.yt) sum = ((ld_state<POL>(v.yt + col[j]) >> lane) & 1u) ? -v.ym : v.ym;
+    else sum = ld_state<POL>(v.lp + int64_t(col[j]) * kLanes);
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) sum += g[j][k];
+    if ((v.act >> lane) & 1u) v.lv[int64_t(col[j]) * kLanes] = sum;
+    const uint32_t hard = __ballot_sync(kFull, sum < M(0));
+    if (lane == 0) {
+      uint32_t* px = v.xh + col[j];
+      *px = v.act == kFull ? hard : (ld_state<POL>(px) & ~v.act) | (hard & v.act);
+    }
+  }
 }
 
 // The variable-node update of node `col` of the view's tile, by one warp: the

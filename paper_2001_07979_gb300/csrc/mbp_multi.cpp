@@ -112,7 +112,8 @@ struct Groups {
 // ---- kernel launches of one batch, by message type
 struct Kernels {
   cudaError_t (*group_step)(const DevCode&, const DevState&, int, double, cudaStream_t);
-  cudaError_t (*build_lists)(const MultiTables&, const MultiShape&, int, int, unsigned long long, cudaStream_t);
+  cudaError_t (*build_lists)(const MultiTables&, const MultiShape&, int, int, unsigned long long, const GroupConds&,
+                             cudaStream_t);
   cudaError_t (*check)(const MultiTables&, const MultiShape&, int, const MultiTuning&, int, cudaStream_t);
   cudaError_t (*variable)(const MultiTables&, const MultiShape&, const MultiTuning&, int, cudaStream_t);
   cudaError_t (*syndrome)(const MultiTables&, const MultiShape&, int, const MultiTuning&, int, cudaStream_t);
@@ -132,98 +133,171 @@ Kernels kernels_of(int msg_dtype) {
   }
 }
 
+const GroupConds kNoConds{0, {}};
+
 // The test before iteration 1 (lists of every tile, syndrome test, retirement at t = 0).
 cudaError_t issue_prologue(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu,
-                           int sms, int in_graph, unsigned long long h, cudaStream_t s) {
+                           int sms, int in_graph, unsigned long long h, const GroupConds& gc, cudaStream_t s) {
   cudaError_t e;
-  if ((e = k.build_lists(tb, sh, 0, 0, 0, s)) != cudaSuccess) return e;
+  if ((e = k.build_lists(tb, sh, 0, 0, 0, kNoConds, s)) != cudaSuccess) return e;
   for (int c = 0; c < sh.n_cls; ++c)
     if ((e = k.syndrome(tb, sh, c, tu, sms, s)) != cudaSuccess) return e;
-  return k.build_lists(tb, sh, 1, in_graph, h, s);
+  return k.build_lists(tb, sh, 1, in_graph, h, gc, s);
 }
 
-// One iteration: eq. (6) per class, eq. (2), the stopping test per class, retirement (persistent kernels);
-// or every group's streaming-schedule kernels, then retirement (grid kernels, first_iter fixed at capture).
-cudaError_t issue_iteration(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu,
-                            int sms, int in_graph, unsigned long long h, const Groups& gs, int first_iter,
-                            cudaStream_t s) {
+// One iteration's decoding work: eq. (6) per class, eq. (2), the stopping test per class (persistent kernels);
+// or every group's streaming-schedule kernels (grid kernels, first_iter fixed at capture).
+cudaError_t issue_work(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu,
+                       int sms, const Groups& gs, int first_iter, cudaStream_t s) {
   cudaError_t e;
   if (tu.grid) {
     for (size_t g = 0; g < gs.code.size(); ++g) {
       if (gs.st[g].F == 0) continue;
       if ((e = k.group_step(gs.code[g], gs.st[g], first_iter, gs.l_max, s)) != cudaSuccess) return e;
     }
-  } else {
-    prof_begin(MBP_KERNEL_CHECK, s);
-    for (int c = 0; c < sh.n_cls; ++c)
-      if ((e = k.check(tb, sh, c, tu, sms, s)) != cudaSuccess) return e;
-    prof_end(MBP_KERNEL_CHECK, s, sh.n_cls);
-    prof_begin(MBP_KERNEL_VARIABLE, s);
-    if ((e = k.variable(tb, sh, tu, sms, s)) != cudaSuccess) return e;
-    prof_end(MBP_KERNEL_VARIABLE, s, 1);
-    prof_begin(MBP_KERNEL_SYNDROME, s);
-    for (int c = 0; c < sh.n_cls; ++c)
-      if ((e = k.syndrome(tb, sh, c, tu, sms, s)) != cudaSuccess) return e;
-    prof_end(MBP_KERNEL_SYNDROME, s, sh.n_cls);
+    return cudaSuccess;
   }
+  prof_begin(MBP_KERNEL_CHECK, s);
+  for (int c = 0; c < sh.n_cls; ++c)
+    if ((e = k.check(tb, sh, c, tu, sms, s)) != cudaSuccess) return e;
+  prof_end(MBP_KERNEL_CHECK, s, sh.n_cls);
+  prof_begin(MBP_KERNEL_VARIABLE, s);
+  if ((e = k.variable(tb, sh, tu, sms, s)) != cudaSuccess) return e;
+  prof_end(MBP_KERNEL_VARIABLE, s, 1);
+  prof_begin(MBP_KERNEL_SYNDROME, s);
+  for (int c = 0; c < sh.n_cls; ++c)
+    if ((e = k.syndrome(tb, sh, c, tu, sms, s)) != cudaSuccess) return e;
+  prof_end(MBP_KERNEL_SYNDROME, s, sh.n_cls);
+  return cudaSuccess;
+}
+
+cudaError_t issue_retire(const Kernels& k, const MultiTables& tb, const MultiShape& sh, int in_graph,
+                         unsigned long long h, const GroupConds& gc, cudaStream_t s) {
   prof_begin(MBP_KERNEL_RETIRE, s);
-  e = k.build_lists(tb, sh, 1, in_graph, h, s);
+  const cudaError_t e = k.build_lists(tb, sh, 1, in_graph, h, gc, s);
   prof_end(MBP_KERNEL_RETIRE, s, 1);
   return e;
 }
 
-// The whole loop as one graph: the prologue, then (grid kernels) iteration 1, then a WHILE node whose body is
-// one iteration. With the grid kernels iteration 1 runs even when nothing is left to decode: every tile is
-// then retired and its blocks return at once.
+// Grid kernels: one IF node per group with frames (parallel branches, each running its group's step while the
+// group has unfinished tiles), all depending on `deps`; returns the IF nodes.
+int add_group_branches(const Kernels& k, const Groups& gs, const GroupConds& gc, int first_iter, cudaGraph_t graph,
+                       const std::vector<cudaGraphNode_t>& deps, cudaStream_t cs,
+                       std::vector<cudaGraphNode_t>* nodes) {
+  cudaError_t e;
+  for (size_t g = 0; g < gs.code.size(); ++g) {
+    if (gs.st[g].F == 0) continue;
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = gc.h[g];
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, graph, deps.data(), nullptr, deps.size(), &p)) != cudaSuccess)
+      return cuda_error(e, "cudaGraphAddNode (IF)");
+    cudaGraph_t sub = p.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, sub, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      return cuda_error(e, "begin capture (group step)");
+    const cudaError_t ke = k.group_step(gs.code[g], gs.st[g], first_iter, gs.l_max, cs);
+    cudaGraph_t out = sub;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &out);
+    if (ke != cudaSuccess) return cuda_error(ke, "group step during capture");
+    if (ee != cudaSuccess) return cuda_error(ee, "end capture (group step)");
+    nodes->push_back(node);
+  }
+  return MBP_OK;
+}
+
+// Capture `issue` into `graph` after `deps`; *leaf gets the captured work's last nodes.
+template <typename F>
+int capture_after(cudaGraph_t graph, const std::vector<cudaGraphNode_t>& deps, cudaStream_t cs, F issue,
+                  std::vector<cudaGraphNode_t>* leaf, const char* what) {
+  cudaError_t e;
+  if ((e = cudaStreamBeginCaptureToGraph(cs, graph, deps.data(), nullptr, deps.size(),
+                                         cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_error(e, what);
+  const cudaError_t ie = issue(cs);
+  cudaStreamCaptureStatus status;
+  const cudaGraphNode_t* d = nullptr;
+  size_t nd = 0;
+  const cudaError_t qe = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &d, nullptr, &nd);
+  if (leaf) leaf->assign(d, d + (qe == cudaSuccess ? nd : 0));
+  cudaGraph_t out = graph;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &out);
+  if (ie != cudaSuccess) return cuda_error(ie, what);
+  if (qe != cudaSuccess) return cuda_error(qe, "cudaStreamGetCaptureInfo");
+  if (ee != cudaSuccess) return cuda_error(ee, what);
+  return MBP_OK;
+}
+
+// The whole loop as one graph. Persistent kernels: the prologue, then a WHILE node whose body is one
+// iteration. Grid kernels: the prologue, iteration 1, then WHILE{iteration}, where each iteration is one IF
+// node per group (its step runs only while the group has unfinished tiles; the groups run as parallel
+// branches) followed by the retire kernel, which sets the WHILE and IF conditions for the next iteration.
 int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu, int sms,
                 const Groups& gs, cudaGraphExec_t* out) {
   cudaError_t e;
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
   int rc = MBP_OK;
+  GroupConds ga{0, {}}, gb{0, {}};  // IF conditions of iteration 1 and of the loop body
+  std::vector<cudaGraphNode_t> leaf, branches;
 #define GK(call, what)                 \
   if ((e = (call)) != cudaSuccess) {   \
     rc = cuda_error(e, what);          \
     goto done;                         \
   }
+#define GR(call)           \
+  if ((rc = (call))) goto done;
   {
     GK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
     GK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
     cudaGraphConditionalHandle h;
     GK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault), "cudaGraphConditionalHandleCreate");
-    GK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
-       "begin capture (prologue)");
-    {
-      cudaError_t pe = issue_prologue(k, tb, sh, tu, sms, 1, h, cs);
-      if (pe == cudaSuccess && tu.grid) pe = issue_iteration(k, tb, sh, tu, sms, 1, h, gs, 1, cs);
-      cudaStreamCaptureStatus status;
-      const cudaGraphNode_t* deps = nullptr;
-      size_t nd = 0;
-      const cudaError_t ie = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &nd);
-      std::vector<cudaGraphNode_t> leaf(deps, deps + (ie == cudaSuccess ? nd : 0));
-      cudaGraph_t captured = g;
-      const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
-      GK(pe, "prologue launch during capture");
-      GK(ie, "cudaStreamGetCaptureInfo");
-      GK(ee, "end capture (prologue)");
-      cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-      p.conditional.handle = h;
-      p.conditional.type = cudaGraphCondTypeWhile;
-      p.conditional.size = 1;
-      cudaGraphNode_t cnode;
-      GK(cudaGraphAddNode(&cnode, g, leaf.data(), nullptr, leaf.size(), &p), "cudaGraphAddNode (WHILE)");
-      cudaGraph_t body = p.conditional.phGraph_out[0];
-      GK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
-         "begin capture (loop body)");
-      const cudaError_t be = issue_iteration(k, tb, sh, tu, sms, 1, h, gs, 0, cs);
-      cudaGraph_t body_out = body;
-      const cudaError_t ebe = cudaStreamEndCapture(cs, &body_out);
-      GK(be, "loop body launch during capture");
-      GK(ebe, "end capture (loop body)");
-      GK(cudaGraphInstantiate(out, g, 0), "cudaGraphInstantiate");
+    if (tu.grid) {
+      ga.n = gb.n = int(gs.code.size());
+      for (size_t q = 0; q < gs.code.size(); ++q) {
+        ga.h[q] = gb.h[q] = ~0ull;
+        if (gs.st[q].F == 0) continue;
+        cudaGraphConditionalHandle ha, hb;
+        GK(cudaGraphConditionalHandleCreate(&ha, g, 1, cudaGraphCondAssignDefault), "conditional handle (IF)");
+        GK(cudaGraphConditionalHandleCreate(&hb, g, 1, cudaGraphCondAssignDefault), "conditional handle (IF)");
+        ga.h[q] = ha;
+        gb.h[q] = hb;
+      }
     }
+    GR(capture_after(g, {}, cs, [&](cudaStream_t st) { return issue_prologue(k, tb, sh, tu, sms, 1, h, ga, st); },
+                     &leaf, "capture (prologue)"));
+    if (tu.grid) {  // iteration 1
+      branches.clear();
+      GR(add_group_branches(k, gs, ga, 1, g, leaf, cs, &branches));
+      GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, 1, h, gb, st); },
+                       &leaf, "capture (retire)"));
+    }
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    GK(cudaGraphAddNode(&cnode, g, leaf.data(), nullptr, leaf.size(), &p), "cudaGraphAddNode (WHILE)");
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    if (tu.grid) {
+      branches.clear();
+      GR(add_group_branches(k, gs, gb, 0, body, {}, cs, &branches));
+      GR(capture_after(body, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, 1, h, gb, st); },
+                       nullptr, "capture (loop body)"));
+    } else {
+      GR(capture_after(body, {}, cs,
+                       [&](cudaStream_t st) {
+                         cudaError_t we = issue_work(k, tb, sh, tu, sms, gs, 0, st);
+                         return we != cudaSuccess ? we : issue_retire(k, tb, sh, 1, h, kNoConds, st);
+                       },
+                       nullptr, "capture (loop body)"));
+    }
+    GK(cudaGraphInstantiate(out, g, 0), "cudaGraphInstantiate");
   }
 done:
+#undef GR
 #undef GK
   if (g) cudaGraphDestroy(g);
   if (cs) cudaStreamDestroy(cs);
@@ -404,15 +478,16 @@ int run_multi(const mbp_group* g, int G, int max_iter, const mbp_opts* o, bool h
     // host-driven loop: the same kernels, one launch each, with a read-back of the loop condition
     int32_t cond = 0;
     prof_begin(MBP_KERNEL_RETIRE, s);
-    if ((e = issue_prologue(k, tb, sh, tu, sms, 0, 0, s)) != cudaSuccess) return cuda_error(e, "grouped prologue");
+    if ((e = issue_prologue(k, tb, sh, tu, sms, 0, 0, kNoConds, s)) != cudaSuccess)
+      return cuda_error(e, "grouped prologue");
     prof_end(MBP_KERNEL_RETIRE, s, 2 + sh.n_cls);
     for (int t = 1;; ++t) {
       if ((e = cudaMemcpyAsync(&cond, &tb.ctl->cond, sizeof cond, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_error(e, "read loop condition");
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
       if (!cond) break;
-      if ((e = issue_iteration(k, tb, sh, tu, sms, 0, 0, gs, t == 1, s)) != cudaSuccess)
-        return cuda_error(e, "grouped iteration");
+      if ((e = issue_work(k, tb, sh, tu, sms, gs, t == 1, s)) != cudaSuccess) return cuda_error(e, "grouped iteration");
+      if ((e = issue_retire(k, tb, sh, 0, 0, kNoConds, s)) != cudaSuccess) return cuda_error(e, "grouped retire");
     }
   } else {
     cudaGraphExec_t exec = nullptr;

@@ -181,8 +181,11 @@ constexpr int64_t kOne = int64_t(1) << kCountShift;
 __global__ void __launch_bounds__(1024) lists_kernel(MultiGroup* __restrict__ gr, MultiCtl* __restrict__ ctl,
                                                      const int32_t* __restrict__ tile_group, int T, int n_cls,
                                                      int32_t* __restrict__ lists, int64_t* __restrict__ pre,
-                                                     int retire, int in_graph, unsigned long long cond_handle) {
+                                                     int retire, int in_graph, unsigned long long cond_handle,
+                                                     const __grid_constant__ GroupConds gc) {
   __shared__ int64_t sh[32];
+  __shared__ int g_active[kMaxGroups];  // groups with an unfinished tile (for the per-group conditions)
+  for (int g = threadIdx.x; g < gc.n; g += blockDim.x) g_active[g] = 0;
   __shared__ int64_t carry[kMaxClasses + 1];  // class k: count << 47 | rows; [n_cls]: count << 47 | nodes
   __shared__ int64_t carry_syn[kMaxClasses];
   const int t = ctl->t, max_iter = ctl->max_iter, early = ctl->early_exit;
@@ -201,6 +204,7 @@ __global__ void __launch_bounds__(1024) lists_kernel(MultiGroup* __restrict__ gr
                                  G.success, G.synd_ok)
                    : G.st.active[tile];
       if (act) {
+        if (gc.n) g_active[tile_group[gt]] = 1;
         cls = G.cls;
         rows = G.c.m_tot;
         synw = (G.c.m_tot + 31) >> 5;
@@ -248,6 +252,11 @@ __global__ void __launch_bounds__(1024) lists_kernel(MultiGroup* __restrict__ gr
       if (in_graph) cudaGraphSetConditional(cond_handle, unsigned(cond));
     }
   }
+  if (gc.n) {
+    __syncthreads();
+    for (int g = threadIdx.x; g < gc.n; g += blockDim.x)
+      if (gc.h[g] != ~0ull) cudaGraphSetConditional(gc.h[g], unsigned(g_active[g]));  // ~0: group without frames
+  }
 }
 
 // Persistent launch: (resident blocks per SM / waves) x SMs blocks.
@@ -271,9 +280,9 @@ cudaError_t persist(void (*kern)(P...), int threads, int waves, int sms, cudaStr
 
 template <typename S>
 cudaError_t MultiLaunch<S>::build_lists(const MultiTables& tb, const MultiShape& sh, int retire, int in_graph,
-                                        unsigned long long cond_handle, cudaStream_t s) {
+                                        unsigned long long cond_handle, const GroupConds& gc, cudaStream_t s) {
   multi::lists_kernel<<<1, 1024, 0, s>>>(tb.groups, tb.ctl, tb.tile_group, sh.T, sh.n_cls, tb.lists, tb.pre, retire,
-                                         in_graph, cond_handle);
+                                         in_graph, cond_handle, gc);
   return cudaGetLastError();
 }
 

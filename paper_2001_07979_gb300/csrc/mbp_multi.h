@@ -74,6 +74,13 @@ struct MultiTables {
   int64_t* pre;         // [2 n_cls + 1][T + 1]: rows per class, syndrome warps per class, nodes (all)
 };
 
+// The conditions of the per-group IF nodes of a graph (grid kernels): group g's step runs while it has
+// unfinished tiles. n = 0: no per-group conditions.
+struct GroupConds {
+  int32_t n;
+  unsigned long long h[kMaxGroups];
+};
+
 struct MultiShape {
   int G, T, n_cls;
   int cls_dmax[kMaxClasses];  // unroll bound of each class slot
@@ -83,7 +90,7 @@ struct MultiShape {
 template <typename S>
 struct MultiLaunch {
   static cudaError_t build_lists(const MultiTables& tb, const MultiShape& sh, int retire, int in_graph,
-                                 unsigned long long cond_handle, cudaStream_t s);
+                                 unsigned long long cond_handle, const GroupConds& gc, cudaStream_t s);
   static cudaError_t check(const MultiTables& tb, const MultiShape& sh, int cls, const MultiTuning& tu, int sms,
                            cudaStream_t s);
   static cudaError_t variable(const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu, int sms,

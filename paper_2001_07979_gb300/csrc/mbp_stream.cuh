@@ -27,10 +27,19 @@ using namespace dev;
 
 inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
+// Resident blocks of 256 threads the check kernel is compiled for: 5 per SM (48
+// registers, no spills) for float rows of up to 14 edges, more latency hiding
+// than the 4 that 64 registers allow; longer rows (and FP64) keep the
+// compiler's choice.
+template <typename M>
+constexpr int cn_min_blocks(int dmax) {
+  return sizeof(M) == 4 && dmax <= 14 ? 5 : 1;
+}
+
 // One warp per (tile, check row): 8 rows per block, tile = blockIdx.y, rows
 // p0 .. p1 - 1 (every row for flooding, one matrix's rows for the serial order).
 template <typename M, typename S, int DMAX, bool FIXED>
-__global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int p0, int p1, int first_iter,
+__global__ void __launch_bounds__(256, cn_min_blocks<M>(DMAX)) cn_kernel(const DevCode c, int p0, int p1, int first_iter,
                                                  S* __restrict__ c2v, const M* __restrict__ lsrc,
                                                  const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                                  const uint32_t* __restrict__ zt,
@@ -43,6 +52,32 @@ __global__ void __launch_bounds__(256) cn_kernel(const DevCode c, int p0, int p1
   if (p >= p1) return;
   cn_tile_row<M, S, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, yt, ymag, zt, l_max,
                                           M(1) / l_max, lacc, qscale);
+}
+
+// Iteration 1 of BSC inputs in a kernel of its own (sign words in, messages
+// out; far fewer registers than cn_kernel, so more warps keep writes in flight).
+template <typename M, typename S, int DMAX>
+__global__ void __launch_bounds__(256) cn_first_kernel(const DevCode c, int p0, int p1, S* __restrict__ c2v,
+                                                       const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
+                                                       const uint32_t* __restrict__ zt,
+                                                       const uint32_t* __restrict__ active, M l_max) {
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= p1) return;
+  const int lane = threadIdx.x & 31;
+  const int base = c.slice_base[p];
+  const int deg = c.slice_base[p + 1] - base;
+  const int* cols = c.slot_col + base;
+  const uint32_t par = ((zt[int64_t(tile) * c.m_tot + p] >> lane) & 1u) << 31;
+  const bool store = (act >> lane) & 1u;
+  const M ym = __ldg(ymag + tile * kLanes + lane);
+  S* msg = c2v + (int64_t(tile) * c.s_tot + base) * kLanes + lane;
+  const uint32_t* ysrc = yt + int64_t(tile) * c.n;
+  const M inv = M(1) / l_max;
+  if (deg == DMAX) cn_row_signs<M, S, DMAX, false, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
+  else cn_row_signs<M, S, DMAX, true, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
 }
 
 // The min-sum check rule (variant), FP32 arithmetic; same layout as cn_kernel.
@@ -76,9 +111,10 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __res
   vn_node<M, S, kPolStream>(c, tile, col, act, c2v, lv, lp, yt, ymag, xh);
 }
 
-// The same update for the nodes of one degree class (DevCode::vclass_*): the
-// node and its slots are loaded together, one dependent round trip fewer.
-template <typename M, typename S>
+// The same update for the nodes of one degree class (DevCode::vclass_*): a
+// node and its slots are loaded together (one dependent round trip fewer), and
+// a warp takes N nodes of degree <= D so that about 16 gathers are in flight.
+template <typename M, typename S, int D, int N>
 __global__ void __launch_bounds__(256) vn_class_kernel(const DevCode c, int cls, const S* __restrict__ c2v,
                                                        M* __restrict__ lv, const M* __restrict__ lp,
                                                        const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
@@ -87,24 +123,35 @@ __global__ void __launch_bounds__(256) vn_class_kernel(const DevCode c, int cls,
   const int tile = blockIdx.y;
   const uint32_t act = active[tile];
   if (act == 0) return;
-  const int first = c.vclass_first[cls];
-  const int qq = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (qq >= c.vclass_first[cls + 1] - first) return;
+  const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
+  const int qq = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
+  if (qq >= count) return;
   const int d = c.vclass_deg[cls];
-  const int col = __ldg(c.vnode + first + qq);
+  const VnView<M, S> v = vn_view<M, S, kPolStream>(c, tile, act, c2v, lv, lp, yt, ymag, xh);
   const int32_t* slots = c.vslot + c.vclass_toff[cls] + int64_t(qq) * d;
-  vn_core<M, S, kPolStream>(vn_view<M, S, kPolStream>(c, tile, act, c2v, lv, lp, yt, ymag, xh), col, slots, d);
+  if constexpr (D > 16) {  // long nodes: one per warp, 16 edges at a time
+    vn_core<M, S, kPolStream>(v, __ldg(c.vnode + first + qq), slots, d);
+  } else {
+    vn_class_nodes<M, S, D, N, kPolStream>(v, c.vnode, first + qq, slots, d, min(N, count - qq));
+  }
 }
 
 // Eq. (2) for every node of every unfinished tile: one launch per degree class, or one over all nodes.
 template <typename M, typename S>
 void launch_vn(const DevCode& c, const DevState& st, cudaStream_t s) {
   if (c.n_vclass > 0) {
-    for (int k = 0; k < c.n_vclass; ++k)
-      vn_class_kernel<M, S><<<dim3(blocks_for(c.vclass_first[k + 1] - c.vclass_first[k], 8), st.n_tiles), 256, 0,
-                              s>>>(c, k, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv),
-                                   static_cast<const M*>(st.lp), st.yt, static_cast<const M*>(st.chan_mag), st.xh,
-                                   st.active);
+    for (int k = 0; k < c.n_vclass; ++k) {
+      const int count = c.vclass_first[k + 1] - c.vclass_first[k], d = c.vclass_deg[k];
+#define MBP_VN(D, N)                                                                                        \
+  vn_class_kernel<M, S, D, N><<<dim3(blocks_for(count, 8 * N), st.n_tiles), 256, 0, s>>>(                  \
+      c, k, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv), static_cast<const M*>(st.lp), st.yt,     \
+      static_cast<const M*>(st.chan_mag), st.xh, st.active)
+      if (d <= 4) MBP_VN(4, 4);
+      else if (d <= 8) MBP_VN(8, 2);
+      else if (d <= 16) MBP_VN(16, 1);
+      else MBP_VN(64, 1);
+#undef MBP_VN
+    }
   } else {
     vn_kernel<M, S><<<dim3(blocks_for(c.n, 8), st.n_tiles), 256, 0, s>>>(
         c, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv), static_cast<const M*>(st.lp), st.yt,
@@ -171,6 +218,14 @@ template <typename M, typename S, int DMAX, bool FIXED>
 void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l_max, float qscale, int rule,
                cudaStream_t s) {
   const dim3 grid(blocks_for(q.p1 - q.p0, 8), st.n_tiles);
+  if constexpr (!FIXED && DMAX <= 32) {
+    if (q.first_iter && q.yt && rule == MBP_RULE_SUM_PRODUCT) {
+      cn_first_kernel<M, S, DMAX><<<grid, 256, 0, s>>>(c, q.p0, q.p1, static_cast<S*>(st.c2v), q.yt,
+                                                       static_cast<const M*>(st.chan_mag), st.zt, st.active,
+                                                       M(l_max));
+      return;
+    }
+  }
   if constexpr (sizeof(M) == 4 && !FIXED) {
     if (rule == MBP_RULE_MIN_SUM) {
       cn_minsum_kernel<S, DMAX><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
