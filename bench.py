@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """Throughput of batched multi-matrix BP reconciliation on GB300.
 
-One step = one mbp_decode_bsc call that reconciles a batch of BSC frames:
+One step = one mbp_decode_bsc call that reconciles a batch of BSC frames (by
+default with the graph schedule: the iteration loop inside one CUDA graph):
 n = 65536 bits per frame, u = 2 PEG matrices of rate 0.7 (m = 19661 each),
 variable degrees {2: 30%, 3: 40%, 8: 30%}, QBER 2%, 1024 frames, at most 60
 flooding iterations, FP32 messages. Frames are synthetic (seeded), the codes
@@ -56,7 +57,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--accumulate", default="auto", choices=["auto", "float", "fixed"],
                    help="eq. (2) accumulation: fixed-point single pass or float second pass")
-    p.add_argument("--schedule", default="auto", choices=["auto", "streaming", "resident", "graph"],
+    p.add_argument("--schedule", default="graph", choices=["auto", "streaming", "resident", "graph"],
                    help="kernels per iteration, one cooperative launch keeping tile groups in L2, or persistent "
                         "kernels with the iteration loop in a CUDA graph")
     p.add_argument("--rule", default="sum-product", choices=["sum-product", "min-sum"],

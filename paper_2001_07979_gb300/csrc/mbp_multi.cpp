@@ -171,10 +171,11 @@ cudaError_t issue_work(const Kernels& k, const MultiTables& tb, const MultiShape
   return cudaSuccess;
 }
 
-cudaError_t issue_retire(const Kernels& k, const MultiTables& tb, const MultiShape& sh, int in_graph,
-                         unsigned long long h, const GroupConds& gc, cudaStream_t s) {
+// Retirement after an iteration; the grid kernels need no lists (retire mode 2).
+cudaError_t issue_retire(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu,
+                         int in_graph, unsigned long long h, const GroupConds& gc, cudaStream_t s) {
   prof_begin(MBP_KERNEL_RETIRE, s);
-  const cudaError_t e = k.build_lists(tb, sh, 1, in_graph, h, gc, s);
+  const cudaError_t e = k.build_lists(tb, sh, tu.grid ? 2 : 1, in_graph, h, gc, s);
   prof_end(MBP_KERNEL_RETIRE, s, 1);
   return e;
 }
@@ -271,7 +272,7 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
     if (tu.grid) {  // iteration 1
       branches.clear();
       GR(add_group_branches(k, gs, ga, 1, g, leaf, cs, &branches));
-      GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, 1, h, gb, st); },
+      GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, gb, st); },
                        &leaf, "capture (retire)"));
     }
     cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
@@ -284,13 +285,13 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
     if (tu.grid) {
       branches.clear();
       GR(add_group_branches(k, gs, gb, 0, body, {}, cs, &branches));
-      GR(capture_after(body, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, 1, h, gb, st); },
+      GR(capture_after(body, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, gb, st); },
                        nullptr, "capture (loop body)"));
     } else {
       GR(capture_after(body, {}, cs,
                        [&](cudaStream_t st) {
                          cudaError_t we = issue_work(k, tb, sh, tu, sms, gs, 0, st);
-                         return we != cudaSuccess ? we : issue_retire(k, tb, sh, 1, h, kNoConds, st);
+                         return we != cudaSuccess ? we : issue_retire(k, tb, sh, tu, 1, h, kNoConds, st);
                        },
                        nullptr, "capture (loop body)"));
     }
@@ -487,7 +488,7 @@ int run_multi(const mbp_group* g, int G, int max_iter, const mbp_opts* o, bool h
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
       if (!cond) break;
       if ((e = issue_work(k, tb, sh, tu, sms, gs, t == 1, s)) != cudaSuccess) return cuda_error(e, "grouped iteration");
-      if ((e = issue_retire(k, tb, sh, 0, 0, kNoConds, s)) != cudaSuccess) return cuda_error(e, "grouped retire");
+      if ((e = issue_retire(k, tb, sh, tu, 0, 0, kNoConds, s)) != cudaSuccess) return cuda_error(e, "grouped retire");
     }
   } else {
     cudaGraphExec_t exec = nullptr;

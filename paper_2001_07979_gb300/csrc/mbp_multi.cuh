@@ -174,7 +174,8 @@ constexpr int64_t kOne = int64_t(1) << kCountShift;
 // One block of 1024 threads. retire = 1: close iteration ctl->t (retire the
 // lanes that satisfied every syndrome, or all lanes at max_iter), advance t and
 // set the loop condition (also the WHILE node's, inside a graph). retire = 0:
-// only build the lists of the tiles still active. Lists follow global tile
+// only build the lists of the tiles still active. retire = 2: retire and set
+// the conditions without rebuilding the lists (the grid kernels need none). Lists follow global tile
 // order: list k (k < n_cls) holds the unfinished tiles of class k with prefix
 // sums of their rows (pre[k]) and syndrome warps (pre[n_cls + k]); list n_cls
 // holds every unfinished tile with prefix sums of its nodes (pre[2 n_cls]).
@@ -211,6 +212,10 @@ __global__ void __launch_bounds__(1024) lists_kernel(MultiGroup* __restrict__ gr
         nodes = G.c.n;
       }
     }
+    if (retire == 2) {  // no lists: only whether anything is left
+      if (__syncthreads_or(act != 0) && threadIdx.x == 0) carry[n_cls] |= kOne;
+      continue;
+    }
     for (int k = 0; k <= n_cls; ++k) {
       const bool all = k == n_cls;
       const bool mine = all ? act != 0 : cls == k;
@@ -232,8 +237,9 @@ __global__ void __launch_bounds__(1024) lists_kernel(MultiGroup* __restrict__ gr
       __syncthreads();
     }
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 0; k <= n_cls; ++k) {
+    for (int k = 0; k <= n_cls && retire != 2; ++k) {
       const bool all = k == n_cls;
       const int cnt = int(carry[k] >> kCountShift);
       pre[size_t(all ? 2 * n_cls : k) * Tp + cnt] = carry[k] & kValueMask;
