@@ -409,6 +409,7 @@ int mbp_destroy_codes(mbp_codes* codes) {
   g_err.clear();
   if (!codes) return MBP_OK;
   cudaError_t e = cudaDeviceSynchronize();
+  multi_forget(codes);  // a later handle may get this address
   cudaError_t f = cudaFree(codes->dev_block);
   delete codes;
   if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");

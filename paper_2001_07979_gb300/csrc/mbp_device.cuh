@@ -5,7 +5,8 @@
 // form a tile; every per-edge or per-node array stores the tile's 32 frames of
 // one edge or node contiguously, so each random access moves one 128-byte line
 // (FP32) and one warp (lane = frame) handles one check row or one variable
-// node of one tile.
+// node of one tile. 2-byte messages interleave two tiles per line (msg_at), and
+// their fast kernels (mbp_pair.cuh) give each lane the frame of both tiles.
 //
 // Check-node arithmetic. For a check with incoming V2C values v_k, eq. (6) gives
 //   |C2V_k| = 2 atanh( prod_{r != k} tanh(|v_r| / 2) ),
@@ -147,6 +148,20 @@ struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ __nv_bfloat16 narrow(float v) { return __float2bfloat16_rn(v); }
 };
 
+// Message addressing (the layout of mbp_internal.h): slot k of a tile's row is
+// kMsgStride<S> elements after slot k - 1; 2-byte messages interleave the tiles
+// of a pair, lane by lane.
+template <typename S>
+constexpr int kMsgTiles = sizeof(S) == 2 ? 2 : 1;
+template <typename S>
+constexpr int kMsgStride = kLanes * kMsgTiles<S>;
+// Element of (tile, slot 0, lane).
+template <typename S>
+__device__ __forceinline__ int64_t msg_at(int tile, int s_tot, int lane) {
+  constexpr int P = kMsgTiles<S>;
+  return int64_t(tile / P) * s_tot * kMsgStride<S> + lane * P + tile % P;
+}
+
 // Memory policies.
 //  kPolStream:   streaming kernels, which only read data written by earlier
 //                launches: posterior through the read-only path, messages
@@ -239,7 +254,7 @@ __device__ __forceinline__ void cn_row_signs(int deg, const int* __restrict__ co
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (!CHECKED || k < deg)
-      st_msg<POL>(msg + k * kLanes, Store<S>::narrow(Bits<M>::copy_sign(mag, par ^ (((bits >> k) & 1u) << 31))));
+      st_msg<POL>(msg + k * kMsgStride<S>, Store<S>::narrow(Bits<M>::copy_sign(mag, par ^ (((bits >> k) & 1u) << 31))));
 }
 
 template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL>
@@ -269,7 +284,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
       for (int k = 0; k < D; ++k)
         if (!CHECKED || col[k] >= 0) {
           const M nv = Bits<M>::copy_sign(mag, par ^ sgn[k]);
-          st_msg<POL>(msg + k * kLanes, Store<S>::narrow(nv));
+          st_msg<POL>(msg + k * kMsgStride<S>, Store<S>::narrow(nv));
           if constexpr (FIXED) {
             const int32_t dq = __float2int_rn(float(nv) * qscale);
             if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
@@ -285,7 +300,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const M o = (!CHECKED || col[k] >= 0) ? M(Store<S>::widen(ld_msg<POL>(msg + k * kLanes))) : M(0);
+      const M o = (!CHECKED || col[k] >= 0) ? M(Store<S>::widen(ld_msg<POL>(msg + k * kMsgStride<S>))) : M(0);
       if constexpr (FIXED) old[k] = o;
       v[k] -= o;
     }
@@ -313,7 +328,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
       const M Dk = Arith<M>::oplus(pre[k], suf);
       const M mag = Arith<M>::clipped_mag(Dk, l_max, inv_l_max);
       const M nv = Bits<M>::copy_sign(mag, par ^ Bits<M>::sign_word(v[k]));
-      st_msg<POL>(msg + k * kLanes, Store<S>::narrow(nv));
+      st_msg<POL>(msg + k * kMsgStride<S>, Store<S>::narrow(nv));
       if constexpr (FIXED) {
         const int32_t dq = __float2int_rn(float(nv) * qscale) - __float2int_rn(float(old[k]) * qscale);
         if (dq != 0) atomicAdd(lacc + col[k] * kLanes, dq);
@@ -368,7 +383,7 @@ __device__ __forceinline__ void cn_row_minsum(int deg, const int* __restrict__ c
   if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      v[k] -= (!CHECKED || col[k] >= 0) ? float(Store<S>::widen(ld_msg<POL>(msg + k * kLanes))) : 0.f;
+      v[k] -= (!CHECKED || col[k] >= 0) ? float(Store<S>::widen(ld_msg<POL>(msg + k * kMsgStride<S>))) : 0.f;
   }
   float m1 = __int_as_float(0x7f800000), m2 = m1;  // +inf
   int i1 = -1;
@@ -389,7 +404,7 @@ __device__ __forceinline__ void cn_row_minsum(int deg, const int* __restrict__ c
   for (int k = 0; k < D; ++k)
     if (!CHECKED || col[k] >= 0) {
       const float mag = fminf(k == i1 ? m2 : m1, l_max);
-      st_msg<POL>(msg + k * kLanes, Store<S>::narrow(Bits<float>::copy_sign(mag, par ^ Bits<float>::sign_word(v[k]))));
+      st_msg<POL>(msg + k * kMsgStride<S>, Store<S>::narrow(Bits<float>::copy_sign(mag, par ^ Bits<float>::sign_word(v[k]))));
     }
 }
 
@@ -419,7 +434,7 @@ __device__ __forceinline__ CnView<M, S> cn_view(const DevCode& c, int tile, uint
   CnView<M, S> v;
   v.slice_base = c.slice_base;
   v.slot_col = c.slot_col;
-  v.msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
+  v.msg = c2v + msg_at<S>(tile, c.s_tot, lane);
   v.gsrc = lsrc + node0;
   v.ysrc = signs ? yt + int64_t(tile) * c.n : nullptr;
   v.ym = signs ? ld_state<POL>(ymag + tile * kLanes + lane) : M(0);
@@ -439,7 +454,7 @@ __device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int fi
   const uint32_t par = ((v.zt[p] >> lane) & 1u) << 31;
   const bool store = (v.act >> lane) & 1u;
   cn_tile_row_src<M, S, DMAX, FIXED, POL>(deg, v.slot_col + base, v.gsrc, v.ysrc, v.ym,
-                                          v.msg + int64_t(base) * kLanes, first_iter, par, store, l_max, inv_l_max,
+                                          v.msg + int64_t(base) * kMsgStride<S>, first_iter, par, store, l_max, inv_l_max,
                                           v.lacc, qscale);
 }
 
@@ -452,7 +467,7 @@ __device__ __forceinline__ void cn_view_row_minsum(const CnView<float, S>& v, in
   const uint32_t par = ((v.zt[p] >> lane) & 1u) << 31;
   const bool store = (v.act >> lane) & 1u;
   const int* cols = v.slot_col + base;
-  S* msg = v.msg + int64_t(base) * kLanes;
+  S* msg = v.msg + int64_t(base) * kMsgStride<S>;
   if (deg == DMAX)
     cn_row_minsum<S, DMAX, false, POL>(deg, cols, v.gsrc, v.ysrc, v.ym, msg, first_iter, par, store, l_max);
   else if (DMAX > 1 && deg == DMAX - 1)
@@ -485,7 +500,7 @@ __device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const 
   M g[D];
 #pragma unroll
   for (int k = 0; k < D; ++k)
-    g[k] = slot[k] >= 0 ? M(Store<S>::widen(ld_msg<POL>(msg + int64_t(slot[k]) * kLanes))) : M(0);
+    g[k] = slot[k] >= 0 ? M(Store<S>::widen(ld_msg<POL>(msg + int64_t(slot[k]) * kMsgStride<S>))) : M(0);
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (slot[k] >= 0) sum += g[k];
@@ -516,7 +531,7 @@ __device__ __forceinline__ VnView<M, S> vn_view(const DevCode& c, int tile, uint
   VnView<M, S> v;
   v.col_ptr = c.col_ptr;
   v.col_slot = c.col_slot;
-  v.msg = c2v + int64_t(tile) * c.s_tot * kLanes + lane;
+  v.msg = c2v + msg_at<S>(tile, c.s_tot, lane);
   v.lv = lv + node0;
   v.lp = lp + node0;
   v.yt = yt ? yt + int64_t(tile) * c.n : nullptr;
@@ -543,7 +558,7 @@ __device__ __forceinline__ void vn_class_nodes(const VnView<M, S>& v, const int3
     for (int k = 0; k < D; ++k) {
       const bool on = j < cnt && k < d;
       const int slot = on ? __ldg(slots0 + j * d + k) : 0;
-      g[j][k] = on ? M(Store<S>::widen(ld_msg<POL>(v.msg + int64_t(slot) * kLanes))) : M(0);
+      g[j][k] = on ? M(Store<S>::widen(ld_msg<POL>(v.msg + int64_t(slot) * kMsgStride<S>))) : M(0);
     }
 #pragma unroll
   for (int j = 0; j < N; ++j) {

@@ -10,7 +10,10 @@
 //     row_local name the matrix and row of each position;
 //   * every per-edge message array is indexed [tile][slot][lane]: kLanes = 32
 //     frames ("lanes") are interleaved, so that one edge of a tile's frames is
-//     one contiguous 128-byte (FP32) vector;
+//     one contiguous 128-byte (FP32) vector. 2-byte messages (FP16/BF16) pair
+//     the tiles 2q and 2q + 1 instead: [q][slot][lane][2], so that one 32-bit
+//     word holds a lane's message in both tiles and one edge of the pair is
+//     again a 128-byte line (an odd tile count gets an unused partner);
 //   * col_ptr/col_slot list, for every variable node, the slots of its edges in
 //     stacked-row order (the order in which eq. (2) sums them).
 #pragma once
@@ -34,6 +37,13 @@ constexpr int kMaxColDeg = 64;  // a variable node's edges over all u matrices
 constexpr int kMaxVClasses = 8;  // variable-node degree classes with slot tables of their own
 constexpr int kMaxQBits = 24;   // fixed-point accumulation: at most 2^-24 resolution
 constexpr int kMinQBits = 12;   // and at least 2^-12
+
+// Tiles that share one message line: 2 for 2-byte messages, else 1.
+constexpr int msg_pair(size_t msg_bytes) { return msg_bytes == 2 ? 2 : 1; }
+// Tiles of message storage for n_tiles tiles (rounded up to whole pairs).
+constexpr size_t msg_tiles(size_t n_tiles, size_t msg_bytes) {
+  return (n_tiles + msg_pair(msg_bytes) - 1) / msg_pair(msg_bytes) * msg_pair(msg_bytes);
+}
 
 struct DevCode {
   int32_t n, u, m_tot;
@@ -67,7 +77,7 @@ struct DevCode {
 // Per-call decoder state carved out of the caller's workspace.
 struct DevState {
   int32_t F, n_tiles;
-  void* c2v;          // [n_tiles][s_tot][kLanes] message type
+  void* c2v;          // [n_tiles][s_tot][kLanes] message type ([n_tiles / 2][s_tot][kLanes][2] for 2 bytes)
   void* lv;           // [n_tiles][n][kLanes] posterior L_V of eq. (2)
   void* lp;           // [n_tiles][n][kLanes] channel LLR L_P of general (LLR) inputs
   uint32_t* yt;       // [n_tiles][n] Bob's bits, bit lane, for BSC inputs; NULL when L_P comes from lp

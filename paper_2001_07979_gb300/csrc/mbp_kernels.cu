@@ -202,7 +202,8 @@ __global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, in
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= c.e_tot) return;
   const int tile = frame / kLanes, lane = frame % kLanes;
-  out[e] = M(Store<S>::widen(c2v[(int64_t(tile) * c.s_tot + c.edge_slot[e]) * kLanes + lane])) * Arith<M>::kToLLR;
+  out[e] = M(Store<S>::widen(c2v[msg_at<S>(tile, c.s_tot, lane) + int64_t(c.edge_slot[e]) * kMsgStride<S>])) *
+           Arith<M>::kToLLR;
 }
 
 // ------------------------------------------------------------- driver
@@ -327,7 +328,7 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
   size_t zw = 0;
   for (int l = 0; l < c.u; ++l) zw += (size_t(c.m[l]) + 31) / 32;
   const size_t sizes[kRegions] = {
-      NT * size_t(c.s_tot) * kLanes * ms,                             // c2v
+      msg_tiles(NT, ms) * size_t(c.s_tot) * kLanes * ms,              // c2v
       NT * size_t(c.n) * kLanes * node_size(msg_dtype),               // lv
       NT * size_t(c.n) * kLanes * node_size(msg_dtype),               // lp
       msg_dtype == MBP_MSG_F32 ? NT * size_t(c.n) * kLanes * 4 : 0,  // lacc

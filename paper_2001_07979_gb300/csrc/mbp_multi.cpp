@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "mbp_multi.h"
@@ -315,6 +316,7 @@ struct GraphEntry {
   double l_max;
   std::vector<const DevCode*> codes;  // the grid kernels take each group's code and state as parameters
   std::vector<int> F;
+  std::vector<DevState> st;  // every group's state as captured (workspace carving, LLR or BSC inputs)
   cudaGraphExec_t exec;
   uint64_t used;
 };
@@ -332,6 +334,12 @@ std::vector<TuneEntry> g_tuned;
 uint64_t g_clock = 0;
 constexpr size_t kMaxGraphs = 16;
 
+static_assert(std::is_trivially_copyable<DevState>::value, "DevState is compared bytewise");
+
+bool same_states(const std::vector<DevState>& a, const std::vector<DevState>& b) {
+  return a.size() == b.size() && (a.empty() || std::memcmp(a.data(), b.data(), a.size() * sizeof(DevState)) == 0);
+}
+
 bool same_shape(const MultiShape& a, const MultiShape& b) {
   if (a.G != b.G || a.T != b.T || a.n_cls != b.n_cls) return false;
   for (int k = 0; k < a.n_cls; ++k)
@@ -347,7 +355,8 @@ int graph_for(const Kernels& k, int device, void* ws, int msg_dtype, const Multi
   std::lock_guard<std::mutex> lock(g_mu);
   for (auto& ge : g_graphs)
     if (ge.device == device && ge.ws == ws && ge.msg_dtype == msg_dtype && same_shape(ge.sh, sh) &&
-        same_tuning(ge.tu, tu) && ge.l_max == gs.l_max && ge.codes == codes && ge.F == F) {
+        same_tuning(ge.tu, tu) && ge.l_max == gs.l_max && ge.codes == codes && ge.F == F &&
+        same_states(ge.st, gs.st)) {
       ge.used = ++g_clock;
       *out = ge.exec;
       return MBP_OK;
@@ -361,7 +370,7 @@ int graph_for(const Kernels& k, int device, void* ws, int msg_dtype, const Multi
     cudaGraphExecDestroy(lru->exec);
     g_graphs.erase(lru);
   }
-  g_graphs.push_back(GraphEntry{device, ws, msg_dtype, sh, tu, gs.l_max, codes, F, exec, ++g_clock});
+  g_graphs.push_back(GraphEntry{device, ws, msg_dtype, sh, tu, gs.l_max, codes, F, gs.st, exec, ++g_clock});
   *out = exec;
   return MBP_OK;
 }
@@ -638,6 +647,20 @@ void multi_release() {
   for (auto& ge : g_graphs) cudaGraphExecDestroy(ge.exec);
   g_graphs.clear();
   g_tuned.clear();
+}
+
+void multi_forget(const mbp_codes* h) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const DevCode* d = &h->d;
+  for (size_t i = g_graphs.size(); i-- > 0;)
+    if (std::find(g_graphs[i].codes.begin(), g_graphs[i].codes.end(), d) != g_graphs[i].codes.end()) {
+      cudaGraphExecDestroy(g_graphs[i].exec);
+      g_graphs.erase(g_graphs.begin() + i);
+    }
+  for (size_t i = g_tuned.size(); i-- > 0;)
+    if (std::find(g_tuned[i].codes.begin(), g_tuned[i].codes.end(), static_cast<const void*>(h)) !=
+        g_tuned[i].codes.end())
+      g_tuned.erase(g_tuned.begin() + i);
 }
 
 }  // namespace mbp

@@ -115,5 +115,7 @@ int multi_decode(const mbp_group* g, int G, int max_iter, const mbp_opts* o, boo
 int multi_autotune(const mbp_group* g, int G, int max_iter, const mbp_opts* o, mbp_tuning* best, cudaStream_t s);
 int multi_set_tuning(const mbp_group* g, int G, const mbp_opts* o, const mbp_tuning* t);
 void multi_release();
+// Drop the cached graphs and tunings that name this code (before its handle is freed).
+void multi_forget(const mbp_codes* h);
 
 }  // namespace mbp

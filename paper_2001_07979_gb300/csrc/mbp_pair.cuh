@@ -1,0 +1,318 @@
+// Streaming kernels of 2-byte message storage (FP16 / BF16 messages, FP32
+// arithmetic). The messages of tiles 2q and 2q + 1 share one 128-byte line per
+// edge (msg_at): one warp takes the pair, each lane the same frame position of
+// both tiles, so every message access is one 32-bit word per lane (a full
+// line per warp) and the row's columns and slots are loaded once for 64 frames.
+// Per frame the arithmetic is that of cn_row / cn_row_signs / vn_class_nodes,
+// in the same order, so a frame's messages and posteriors do not depend on the
+// kernel that produced them.
+//
+// A tile whose frames have all retired (or the missing partner of an odd tile
+// count) is neither read nor written; in a pair with one live tile, a lane
+// writes only the halves of its live frames.
+#pragma once
+
+#include "mbp_device.cuh"
+
+namespace mbp {
+namespace dev {
+
+template <typename S>
+struct Pair;
+
+template <>
+struct Pair<__half> {
+  using T = __half2;
+  static __device__ __forceinline__ float2 widen(T v) { return __half22float2(v); }
+  static __device__ __forceinline__ T narrow(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+template <>
+struct Pair<__nv_bfloat16> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ float2 widen(T v) { return __bfloat1622float2(v); }
+  static __device__ __forceinline__ T narrow(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+// Store a lane's two messages; a retired frame keeps its stored half.
+template <typename S>
+__device__ __forceinline__ void st_pair(typename Pair<S>::T* p, float a, float b, bool s0, bool s1) {
+  if (s0 && s1) {
+    __stcs(p, Pair<S>::narrow(a, b));
+  } else {
+    S* h = reinterpret_cast<S*>(p);
+    if (s0) __stcs(h, Store<S>::narrow(a));
+    if (s1) __stcs(h + 1, Store<S>::narrow(b));
+  }
+}
+
+// Everything a warp needs about the two tiles of pair q for the lane's frames.
+struct PairTiles {
+  int t0, t1;        // tile indices (t1 may be past the last tile)
+  uint32_t a0, a1;   // lanes still decoding (0 for a missing tile)
+  bool s0, s1;       // this lane's frame is still decoding, per tile
+};
+
+__device__ __forceinline__ PairTiles pair_tiles(int q, int n_tiles, const uint32_t* __restrict__ active) {
+  const int lane = threadIdx.x & 31;
+  PairTiles p;
+  p.t0 = 2 * q;
+  p.t1 = 2 * q + 1;
+  p.a0 = active[p.t0];
+  p.a1 = p.t1 < n_tiles ? active[p.t1] : 0u;
+  p.s0 = (p.a0 >> lane) & 1u;
+  p.s1 = (p.a1 >> lane) & 1u;
+  return p;
+}
+
+// The prefix pass of eq. (6) for one frame: the row's sign parity into par,
+// each V2C replaced by its delta carrying the V2C's sign bit, pre[k] the (+)
+// fold of edges 0 .. k - 1 (padding edges fold as 0).
+template <int D, bool CHECKED>
+__device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre)[D], uint32_t& par, float l_max,
+                                             float inv_l_max) {
+  using A = Arith<float>;
+  using B = Bits<float>;
+  float P = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const uint32_t x = B::sign_word(v[k]);
+    par ^= x;
+    float d = A::delta(A::clip_abs(v[k], l_max, inv_l_max));
+    if constexpr (CHECKED) d = k < deg ? d : 0.f;
+    v[k] = B::with_sign(d, x & kSign);
+    pre[k] = P;
+    P = A::oplus(P, d);
+  }
+}
+
+// Eq. (6) for one row of both tiles: V2C = clip(L_V - C2V) (L_V alone in the
+// first iteration of general inputs), prefix / suffix (+) folds per frame,
+// output magnitude and sign as in cn_row. g0 / g1 are the tiles' posteriors at
+// this lane; h0 / h1 say whether a tile has live frames (warp-uniform).
+template <typename S, int D, bool CHECKED>
+__device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ cols, const float* __restrict__ g0,
+                                            const float* __restrict__ g1, bool h0, bool h1,
+                                            typename Pair<S>::T* __restrict__ msg, int first_iter, uint32_t par0,
+                                            uint32_t par1, bool s0, bool s1, float l_max, float inv_l_max) {
+  using A = Arith<float>;
+  using B = Bits<float>;
+  int off[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) off[k] = (!CHECKED || k < deg) ? __ldg(cols + k) * kLanes : 0;
+  float v0[D], v1[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const bool on = !CHECKED || k < deg;
+    v0[k] = on && h0 ? __ldg(g0 + off[k]) : 0.f;
+    v1[k] = on && h1 ? __ldg(g1 + off[k]) : 0.f;
+  }
+  if (!first_iter) {
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (!CHECKED || k < deg) {
+        const float2 o = Pair<S>::widen(__ldcs(msg + k * kLanes));
+        v0[k] -= o.x;
+        v1[k] -= o.y;
+      }
+  }
+  if (!s0 && !s1) return;
+  // tile 0, then tile 1, sharing the prefix array; tile 0's outputs replace its deltas in v0
+  float pre[D];
+  cn_pair_fold<D, CHECKED>(deg, v0, pre, par0, l_max, inv_l_max);
+  float q = 0.f;
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
+    const float d = v0[k];
+    if (!CHECKED || k < deg)
+      v0[k] = B::copy_sign(A::clipped_mag(A::oplus(pre[k], q), l_max, inv_l_max), par0 ^ B::sign_word(d));
+    q = A::oplus(q, fabsf(d));
+  }
+  cn_pair_fold<D, CHECKED>(deg, v1, pre, par1, l_max, inv_l_max);
+  q = 0.f;
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
+    if (!CHECKED || k < deg) {
+      const float m1 = A::clipped_mag(A::oplus(pre[k], q), l_max, inv_l_max);
+      st_pair<S>(msg + k * kLanes, v0[k], B::copy_sign(m1, par1 ^ B::sign_word(v1[k])), s0, s1);
+    }
+    q = A::oplus(q, fabsf(v1[k]));
+  }
+}
+
+// The first iteration of BSC inputs for one row of both tiles (cn_row_signs per
+// frame): Bob's bits of the row as one mask per tile, one output magnitude per
+// row and frame.
+template <typename S, int D, bool CHECKED>
+__device__ __forceinline__ void cn_pair_row_signs(int deg, const int* __restrict__ cols,
+                                                  const uint32_t* __restrict__ y0, const uint32_t* __restrict__ y1,
+                                                  bool h0, bool h1, float ym0, float ym1,
+                                                  typename Pair<S>::T* __restrict__ msg, uint32_t par0,
+                                                  uint32_t par1, bool s0, bool s1, float l_max, float inv_l_max) {
+  static_assert(D <= 32, "one bit per edge");
+  const int lane = threadIdx.x & 31;
+  uint32_t b0 = 0, b1 = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (!CHECKED || k < deg) {
+      const int col = __ldg(cols + k);
+      if (h0) b0 |= ((__ldg(y0 + col) >> lane) & 1u) << k;
+      if (h1) b1 |= ((__ldg(y1 + col) >> lane) & 1u) << k;
+    }
+  if (!s0 && !s1) return;
+  par0 ^= uint32_t(__popc(b0) & 1) << 31;
+  par1 ^= uint32_t(__popc(b1) & 1) << 31;
+  const float m0 = cn_first_mag<float, D, CHECKED>(deg, ym0, l_max, inv_l_max);
+  const float m1 = cn_first_mag<float, D, CHECKED>(deg, ym1, l_max, inv_l_max);
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (!CHECKED || k < deg)
+      st_pair<S>(msg + k * kLanes, Bits<float>::copy_sign(m0, par0 ^ (((b0 >> k) & 1u) << 31)),
+                 Bits<float>::copy_sign(m1, par1 ^ (((b1 >> k) & 1u) << 31)), s0, s1);
+}
+
+// Resident blocks of 256 threads per SM for the pair check kernel: two frames
+// per lane double the row's registers.
+constexpr int cn_pair_min_blocks(int dmax) { return dmax <= 14 ? 4 : (dmax <= 16 ? 3 : 2); }
+
+// One warp per (tile pair, check row): 8 rows per block, pair = blockIdx.y,
+// rows p0 .. p1 - 1.
+template <typename S, int DMAX>
+__global__ void __launch_bounds__(256, cn_pair_min_blocks(DMAX))
+    cn_pair_kernel(const DevCode c, int p0, int p1, int first_iter, S* __restrict__ c2v,
+                   const float* __restrict__ lsrc, const uint32_t* __restrict__ zt,
+                   const uint32_t* __restrict__ active, int n_tiles, float l_max) {
+  const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
+  if ((t.a0 | t.a1) == 0) return;
+  const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= p1) return;
+  const int lane = threadIdx.x & 31;
+  const int base = c.slice_base[p];
+  const int deg = c.slice_base[p + 1] - base;
+  const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
+  const uint32_t par0 = h0 ? ((zt[int64_t(t.t0) * c.m_tot + p] >> lane) & 1u) << 31 : 0u;
+  const uint32_t par1 = h1 ? ((zt[int64_t(t.t1) * c.m_tot + p] >> lane) & 1u) << 31 : 0u;
+  using T = typename Pair<S>::T;
+  T* msg = reinterpret_cast<T*>(c2v) + (int64_t(blockIdx.y) * c.s_tot + base) * kLanes + lane;
+  const float* g0 = lsrc + int64_t(t.t0) * c.n * kLanes + lane;
+  const float* g1 = h1 ? lsrc + int64_t(t.t1) * c.n * kLanes + lane : g0;
+  const int* cols = c.slot_col + base;
+  const float inv = 1.0f / l_max;
+  if (deg == DMAX)
+    cn_pair_row<S, DMAX, false>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv);
+  else if (DMAX > 1 && deg == DMAX - 1)
+    cn_pair_row<S, (DMAX > 1 ? DMAX - 1 : 1), false>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0,
+                                                     t.s1, l_max, inv);
+  else
+    cn_pair_row<S, DMAX, true>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv);
+}
+
+// Iteration 1 of BSC inputs for a tile pair.
+template <typename S, int DMAX>
+__global__ void __launch_bounds__(256) cn_first_pair_kernel(const DevCode c, int p0, int p1, S* __restrict__ c2v,
+                                                            const uint32_t* __restrict__ yt,
+                                                            const float* __restrict__ ymag,
+                                                            const uint32_t* __restrict__ zt,
+                                                            const uint32_t* __restrict__ active, int n_tiles,
+                                                            float l_max) {
+  const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
+  if ((t.a0 | t.a1) == 0) return;
+  const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= p1) return;
+  const int lane = threadIdx.x & 31;
+  const int base = c.slice_base[p];
+  const int deg = c.slice_base[p + 1] - base;
+  const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
+  const uint32_t par0 = h0 ? ((zt[int64_t(t.t0) * c.m_tot + p] >> lane) & 1u) << 31 : 0u;
+  const uint32_t par1 = h1 ? ((zt[int64_t(t.t1) * c.m_tot + p] >> lane) & 1u) << 31 : 0u;
+  const float ym0 = h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
+  const float ym1 = h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
+  using T = typename Pair<S>::T;
+  T* msg = reinterpret_cast<T*>(c2v) + (int64_t(blockIdx.y) * c.s_tot + base) * kLanes + lane;
+  const uint32_t* y0 = yt + int64_t(t.t0) * c.n;
+  const uint32_t* y1 = h1 ? yt + int64_t(t.t1) * c.n : y0;
+  const int* cols = c.slot_col + base;
+  const float inv = 1.0f / l_max;
+  if (deg == DMAX)
+    cn_pair_row_signs<S, DMAX, false>(deg, cols, y0, y1, h0, h1, ym0, ym1, msg, par0, par1, t.s0, t.s1, l_max, inv);
+  else
+    cn_pair_row_signs<S, DMAX, true>(deg, cols, y0, y1, h0, h1, ym0, ym1, msg, par0, par1, t.s0, t.s1, l_max, inv);
+}
+
+// Eq. (2) and the hard decision for N nodes of one degree class (degree d <= D)
+// of both tiles: every gather is one 32-bit word per lane (both tiles' C2V of
+// the edge), the sums run in stacked-row order as in vn_class_nodes.
+template <typename S, int D, int N>
+__global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int cls, const S* __restrict__ c2v,
+                                                            float* __restrict__ lv, const float* __restrict__ lp,
+                                                            const uint32_t* __restrict__ yt,
+                                                            const float* __restrict__ ymag, uint32_t* __restrict__ xh,
+                                                            const uint32_t* __restrict__ active, int n_tiles) {
+  static_assert(D <= 16, "short classes only");
+  const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
+  if ((t.a0 | t.a1) == 0) return;
+  const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
+  const int qq = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
+  if (qq >= count) return;
+  const int lane = threadIdx.x & 31;
+  const int d = c.vclass_deg[cls];
+  const int cnt = min(N, count - qq);
+  const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
+  using T = typename Pair<S>::T;
+  const T* msg = reinterpret_cast<const T*>(c2v) + int64_t(blockIdx.y) * c.s_tot * kLanes + lane;
+  const int32_t* slots0 = c.vslot + c.vclass_toff[cls] + int64_t(qq) * d;
+  int col[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) col[j] = j < cnt ? __ldg(c.vnode + first + qq + j) : 0;
+  T g[N][D];
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const bool on = j < cnt && k < d;
+      const int slot = on ? __ldg(slots0 + j * d + k) : 0;
+      g[j][k] = on ? __ldcs(msg + int64_t(slot) * kLanes) : Pair<S>::narrow(0.f, 0.f);
+    }
+  const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
+  const float ym0 = yt && h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
+  const float ym1 = yt && h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j >= cnt) break;
+    const int v = col[j];
+    float sum0 = 0.f, sum1 = 0.f;
+    if (yt) {
+      if (h0) sum0 = ((__ldg(yt + n0 + v) >> lane) & 1u) ? -ym0 : ym0;
+      if (h1) sum1 = ((__ldg(yt + n1 + v) >> lane) & 1u) ? -ym1 : ym1;
+    } else {
+      if (h0) sum0 = __ldg(lp + (n0 + v) * kLanes + lane);
+      if (h1) sum1 = __ldg(lp + (n1 + v) * kLanes + lane);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) {
+        const float2 w = Pair<S>::widen(g[j][k]);
+        sum0 += w.x;
+        sum1 += w.y;
+      }
+    if (h0) {
+      if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
+      const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);
+      if (lane == 0) {
+        uint32_t* px = xh + n0 + v;
+        *px = t.a0 == kFull ? hard : (__ldg(px) & ~t.a0) | (hard & t.a0);
+      }
+    }
+    if (h1) {
+      if (t.s1) lv[(n1 + v) * kLanes + lane] = sum1;
+      const uint32_t hard = __ballot_sync(kFull, sum1 < 0.f);
+      if (lane == 1) {
+        uint32_t* px = xh + n1 + v;
+        *px = t.a1 == kFull ? hard : (__ldg(px) & ~t.a1) | (hard & t.a1);
+      }
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace mbp

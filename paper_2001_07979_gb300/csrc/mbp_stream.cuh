@@ -18,6 +18,7 @@
 #include <cstdio>
 
 #include "mbp_device.cuh"
+#include "mbp_pair.cuh"
 
 namespace mbp {
 namespace {  // every file that includes this keeps its own copies
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) cn_first_kernel(const DevCode c, int p0, 
   const uint32_t par = ((zt[int64_t(tile) * c.m_tot + p] >> lane) & 1u) << 31;
   const bool store = (act >> lane) & 1u;
   const M ym = __ldg(ymag + tile * kLanes + lane);
-  S* msg = c2v + (int64_t(tile) * c.s_tot + base) * kLanes + lane;
+  S* msg = c2v + msg_at<S>(tile, c.s_tot, lane) + int64_t(base) * kMsgStride<S>;
   const uint32_t* ysrc = yt + int64_t(tile) * c.n;
   const M inv = M(1) / l_max;
   if (deg == DMAX) cn_row_signs<M, S, DMAX, false, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
@@ -142,6 +143,17 @@ void launch_vn(const DevCode& c, const DevState& st, cudaStream_t s) {
   if (c.n_vclass > 0) {
     for (int k = 0; k < c.n_vclass; ++k) {
       const int count = c.vclass_first[k + 1] - c.vclass_first[k], d = c.vclass_deg[k];
+      if constexpr (sizeof(S) == 2) {  // tile pairs for classes of up to 16 edges
+        const unsigned pairs = unsigned((st.n_tiles + 1) / 2);
+#define MBP_VN2(D, N)                                                                                         \
+  vn_class_pair_kernel<S, D, N><<<dim3(blocks_for(count, 8 * N), pairs), 256, 0, s>>>(                        \
+      c, k, static_cast<const S*>(st.c2v), static_cast<float*>(st.lv), static_cast<const float*>(st.lp), st.yt, \
+      static_cast<const float*>(st.chan_mag), st.xh, st.active, st.n_tiles)
+        if (d <= 4) { MBP_VN2(4, 4); continue; }
+        if (d <= 8) { MBP_VN2(8, 2); continue; }
+        if (d <= 16) { MBP_VN2(16, 1); continue; }
+#undef MBP_VN2
+      }
 #define MBP_VN(D, N)                                                                                        \
   vn_class_kernel<M, S, D, N><<<dim3(blocks_for(count, 8 * N), st.n_tiles), 256, 0, s>>>(                  \
       c, k, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv), static_cast<const M*>(st.lp), st.yt,     \
@@ -218,6 +230,20 @@ template <typename M, typename S, int DMAX, bool FIXED>
 void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l_max, float qscale, int rule,
                cudaStream_t s) {
   const dim3 grid(blocks_for(q.p1 - q.p0, 8), st.n_tiles);
+  if constexpr (sizeof(S) == 2 && !FIXED && DMAX <= 24) {  // tile pairs (mbp_pair.cuh)
+    if (rule == MBP_RULE_SUM_PRODUCT) {
+      const dim3 pgrid(grid.x, unsigned((st.n_tiles + 1) / 2));
+      if (q.first_iter && q.yt)
+        cn_first_pair_kernel<S, DMAX><<<pgrid, 256, 0, s>>>(c, q.p0, q.p1, static_cast<S*>(st.c2v), q.yt,
+                                                            static_cast<const float*>(st.chan_mag), st.zt, st.active,
+                                                            st.n_tiles, float(l_max));
+      else
+        cn_pair_kernel<S, DMAX><<<pgrid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
+                                                      static_cast<const float*>(q.lsrc), st.zt, st.active,
+                                                      st.n_tiles, float(l_max));
+      return;
+    }
+  }
   if constexpr (!FIXED && DMAX <= 32) {
     if (q.first_iter && q.yt && rule == MBP_RULE_SUM_PRODUCT) {
       cn_first_kernel<M, S, DMAX><<<grid, 256, 0, s>>>(c, q.p0, q.p1, static_cast<S*>(st.c2v), q.yt,
@@ -358,7 +384,7 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
   };
   const bool serial = a.update == MBP_UPDATE_MATRIX_SERIAL && c.u > 1;
   if (serial && a.max_iter > 0 && left > 0)  // matrices not yet visited in iteration 1 contribute 0 to eq. (2)
-    CK(cudaMemsetAsync(st.c2v, 0, size_t(NT) * c.s_tot * kLanes * sizeof(S), s), "clear messages");
+    CK(cudaMemsetAsync(st.c2v, 0, msg_tiles(NT, sizeof(S)) * c.s_tot * kLanes * sizeof(S), s), "clear messages");
   for (int t = 1; t <= a.max_iter && left > 0; ++t) {
     if (serial) {
       // Algorithm 1's nesting: each matrix's checks, then eq. (2) with its new messages, before the next matrix

@@ -279,3 +279,36 @@ def test_set_tuning_selects_kernels_without_changing_results(mbp, batch):
     with pytest.raises(mbp.MBPError) as ei:
         mbp.mbp_multi_set_tuning([g.arg() for g in batch], dict(cn_warps=16))
     assert ei.value.status == 1
+
+
+def test_graph_cache_keys_on_inputs_and_forgets_freed_codes(mbp, batch):
+    """The cached graph of a batch bakes in every group's state: BSC then LLR inputs on one workspace must
+    each get their own graph, and a code freed and replaced by another (whose handle may reuse the address)
+    must not meet the old code's graph."""
+    arg_b = [g.arg() for g in batch]
+    arg_l = [g.arg(llr=True) for g in batch]
+    ws = torch.empty(mbp.mbp_multi_workspace_size(arg_b, mbp.MSG_F32), dtype=torch.uint8, device="cuda")
+    a = mbp.mbp_decode_multi(arg_b, 30, want_soft=True, workspace=ws)
+    b = mbp.mbp_decode_multi(arg_l, 30, want_soft=True, workspace=ws)
+    fresh = mbp.mbp_decode_multi(arg_l, 30, want_soft=True)
+    torch.cuda.synchronize()
+    for g, oa, ob, of in zip(batch, a, b, fresh):
+        for k in ("x_hat_bits", "iters", "success", "soft"):
+            assert torch.equal(ob[k], of[k]), (g.n, k)
+        for k in ("x_hat_bits", "iters", "success"):
+            assert torch.equal(oa[k], ob[k]), (g.n, k)
+    n, F = 1024, 40
+    ws1 = None
+    for seed in range(4):
+        H = mi.make_codes(n, 512, {3: 1.0}, 2, 100 + seed)
+        codes = mbp.mbp_create_codes(H)
+        x, y, e = mi.bsc_frames(n, F, 0.03, seed=200 + seed)
+        z = mbp.mbp_syndrome(codes, dev(i32(x)))
+        if ws1 is None:
+            ws1 = torch.empty(mbp.mbp_decode_workspace_size(codes, F, mbp.MSG_F32, schedule=mbp.SCHED_GRAPH),
+                              dtype=torch.uint8, device="cuda")
+        og = mbp.mbp_decode_bsc(codes, dev(i32(y)), dev(e), z, 30, schedule=mbp.SCHED_GRAPH, workspace=ws1)
+        os_ = mbp.mbp_decode_bsc(codes, dev(i32(y)), dev(e), z, 30, schedule=mbp.SCHED_STREAMING)
+        for k in ("x_hat_bits", "iters", "success"):
+            assert torch.equal(og[k], os_[k]), (seed, k)
+        del codes, og, os_

@@ -1,0 +1,125 @@
+"""FP16 / BF16 message storage, whose messages pair the tiles 2q and 2q + 1 (one 32-bit word per lane holds
+both tiles' message of an edge), through the C ABI.
+
+Each frame's arithmetic is independent of the other frames: the per-frame outputs of a decode (bits,
+iterations, success, posteriors) must not change, bit for bit, with the batch the frame is decoded in. The
+batches here put a frame alone in a tile (no partner tile), beside a partner tile that retires iterations
+earlier, in an odd tile count and in a ragged last tile. Converged frames must also equal the FP64
+oracle's bits, for BSC and LLR inputs and the matrix-serial order.
+"""
+import numpy as np
+import pytest
+import torch
+
+import mbp_inputs as mi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("x_hat_bits", "iters", "success", "soft")
+
+
+@pytest.fixture(scope="module")
+def mbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_07979_gb300 as m
+    m.build()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def i32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32).view(np.int32)
+
+
+class Mixed:
+    """80 frames = 3 tiles (the last one ragged): the first 32 at QBER 0.5% (they retire after one or two
+    iterations), the rest at 4%."""
+
+    def __init__(self, mbp, n=4000, m=1400, u=2, seed=61):
+        self.n = n
+        self.H = mi.make_codes(n, m, {2: 0.3, 3: 0.4, 8: 0.3}, u, seed)
+        self.e = np.concatenate([np.full(32, 0.005), np.full(48, 0.04)])
+        self.F = len(self.e)
+        self.x, self.y, _ = mi.bsc_frames(n, self.F, self.e, seed=seed + 1)
+        self.codes = mbp.mbp_create_codes(self.H)
+
+    def decode(self, mbp, idx, dt, **kw):
+        idx = np.asarray(idx)
+        z = mbp.mbp_syndrome(self.codes, dev(i32(self.x[idx])))
+        out = mbp.mbp_decode_bsc(self.codes, dev(i32(self.y[idx])), dev(self.e[idx]), z, 40, msg_dtype=dt,
+                                 want_soft=True, **kw)
+        return {k: out[k].cpu().numpy() for k in KEYS}
+
+
+@pytest.fixture(scope="module")
+def mixed(mbp):
+    return Mixed(mbp)
+
+
+@pytest.mark.parametrize("msg", ["f16", "bf16"])
+def test_half_storage_frames_independent_of_batch(mbp, mixed, msg):
+    dt = mbp.MSG_F16 if msg == "f16" else mbp.MSG_BF16
+    full = mixed.decode(mbp, np.arange(mixed.F), dt)
+    its = full["iters"]
+    assert its[:32].max() < its[32:].max()  # the first tile retires before its partner
+    subsets = [np.arange(32), np.arange(32, 80), np.array([40]), np.arange(0, 80, 3), np.arange(79, -1, -1)]
+    for idx in subsets:
+        part = mixed.decode(mbp, idx, dt)
+        for k in KEYS:
+            assert np.array_equal(part[k], full[k][idx]), (msg, k, idx[:4])
+    graph = mixed.decode(mbp, np.arange(mixed.F), dt, schedule=mbp.SCHED_GRAPH)
+    for k in KEYS:
+        assert np.array_equal(graph[k], full[k]), (msg, k)
+
+
+@pytest.mark.parametrize("msg", ["f16", "bf16"])
+def test_half_storage_converged_frames_match_oracle(mbp, mixed, msg):
+    dt = mbp.MSG_F16 if msg == "f16" else mbp.MSG_BF16
+    out = mixed.decode(mbp, np.arange(mixed.F), dt)
+    LP = orc.bsc_llr(mixed.y, mixed.n, mixed.e)
+    ref = orc.decode(mixed.H, LP, orc.syndrome(mixed.H, mixed.x), 40, threads=8)
+    conv = ref["success"].astype(bool) & out["success"].astype(bool)
+    assert conv.sum() >= 75
+    assert np.array_equal(out["x_hat_bits"].view(np.uint32)[conv], ref["x_hat_bits"][conv])
+
+
+@pytest.mark.parametrize("msg", ["f16", "bf16"])
+def test_half_storage_llr_inputs_and_serial_order(mbp, mixed, msg):
+    """General LLR inputs (the first iteration reads L_P through the pair kernel) and the matrix-serial order
+    (row ranges per matrix, messages cleared to 0 first): converged frames equal the oracle's bits."""
+    dt = mbp.MSG_F16 if msg == "f16" else mbp.MSG_BF16
+    LP = orc.bsc_llr(mixed.y, mixed.n, mixed.e)
+    z_orc = orc.syndrome(mixed.H, mixed.x)
+    z = mbp.mbp_syndrome(mixed.codes, dev(i32(mixed.x)))
+    out = mbp.mbp_decode_batch(mixed.codes, dev(LP.astype(np.float32)), z, 40, msg_dtype=dt)
+    ref = orc.decode(mixed.H, LP, z_orc, 40, threads=8)
+    conv = ref["success"].astype(bool) & out["success"].cpu().numpy().astype(bool)
+    assert conv.sum() >= 75
+    assert np.array_equal(out["x_hat_bits"].cpu().numpy().view(np.uint32)[conv], ref["x_hat_bits"][conv])
+    ser = mbp.mbp_decode_bsc(mixed.codes, dev(i32(mixed.y)), dev(mixed.e), z, 40, msg_dtype=dt,
+                             update=mbp.UPDATE_MATRIX_SERIAL)
+    ref_s = orc.decode(mixed.H, LP, z_orc, 40, threads=8, update="matrix-serial")
+    conv = ref_s["success"].astype(bool) & ser["success"].cpu().numpy().astype(bool)
+    assert conv.sum() >= 75
+    assert np.array_equal(ser["x_hat_bits"].cpu().numpy().view(np.uint32)[conv], ref_s["x_hat_bits"][conv])
+
+
+def test_half_storage_first_iteration_messages_odd_tiles(mbp):
+    """After one iteration every exported FP16 message of 70 frames (3 tiles, the third without a partner)
+    is the oracle's C2V rounded to FP16 storage: within half an FP16 unit of the largest clipped message."""
+    n, F = 2000, 70
+    H = mi.make_codes(n, 800, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 62)
+    x, y, e = mi.bsc_frames(n, F, 0.05, seed=63)
+    codes = mbp.mbp_create_codes(H)
+    z = mbp.mbp_syndrome(codes, dev(i32(x)))
+    out = mbp.mbp_decode_bsc(codes, dev(i32(y)), dev(e), z, 1, early_exit=False, msg_dtype=mbp.MSG_F16)
+    ref = orc.decode(H, orc.bsc_llr(y, n, e), orc.syndrome(H, x), 1, early_exit=False, want_c2v=True)["c2v"]
+    for f in (0, 31, 32, 63, 64, 69):
+        c = mbp.mbp_export_c2v(codes, F, out["workspace"], f, mbp.MSG_F16).cpu().numpy()
+        # |C2V| <= l_max = 20 < 32: FP16 spacing <= 2^-6 there, rounding error <= 2^-7, plus FP32 arithmetic
+        assert np.max(np.abs(c - ref[f])) <= 2.0 ** -7 + 1e-3, f
