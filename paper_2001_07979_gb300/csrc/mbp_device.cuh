@@ -55,8 +55,14 @@ __device__ __forceinline__ float lg2_ftz(float x) {
 // Check-node arithmetic in the halved complement form (see the file header).
 // FP32 messages are kept in log2 units inside the decoder (LLR * log2 e), so
 // e^{|v|} is one ex2 and the natural log is one lg2: delta = rcp(1 + ex2(a)),
-// magnitude = lg2((1 - D) * rcp(D)). FP64 keeps natural units and the libm
-// exp/log. kToInternal / kToLLR convert at the boundary (set-up and outputs).
+// magnitude = lg2((1 - D) / D) = lg2(rcp(D) - 1). FP64 keeps natural units and
+// the libm exp/log. kToInternal / kToLLR convert at the boundary (set-up and
+// outputs).
+//
+// The clip of eq. (6)'s inputs and outputs to L = l_max: delta falls with |v|,
+// so delta(min(|v|, L)) = max(delta(|v|), delta(L)), one FMNMX with the row's
+// d_lmax = delta(L); the output clip is one more. In FP32 a rounding-level
+// negative magnitude (D a hair below 1/2) is taken as its absolute value.
 template <typename M>
 struct Arith;
 
@@ -66,15 +72,13 @@ struct Arith<float> {
   static constexpr float kToLLR = 0.69314718055994530942f;      // ln(2)
   static __device__ __forceinline__ float delta(float a) { return rcp_ftz(1.0f + ex2_ftz(a)); }
   static __device__ __forceinline__ float oplus(float p, float d) { return fmaf(d, fmaf(-2.0f, p, 1.0f), p); }
-  static __device__ __forceinline__ float mag(float D) { return lg2_ftz((1.0f - D) * rcp_ftz(D)); }
-  // min(|v|, L) = L * sat(|v| / L) on the FMA pipe (.sat clamps to [0, 1])
-  static __device__ __forceinline__ float clip_abs(float v, float L, float invL) {
-    return __saturatef(fabsf(v) * invL) * L;
+  static __device__ __forceinline__ float mag(float D) { return lg2_ftz(rcp_ftz(D) - 1.0f); }
+  // delta(min(|v|, L)); d_lmax = delta(L)
+  static __device__ __forceinline__ float clipped_delta(float v, float, float d_lmax) {
+    return fmaxf(delta(fabsf(v)), d_lmax);
   }
-  // min(mag(D), L); .sat also maps a rounding-level negative magnitude to +0
-  static __device__ __forceinline__ float clipped_mag(float D, float L, float invL) {
-    return __saturatef(mag(D) * invL) * L;
-  }
+  // min(|mag(D)|, L)
+  static __device__ __forceinline__ float clipped_mag(float D, float L) { return fminf(fabsf(mag(D)), L); }
 };
 
 template <>
@@ -84,10 +88,8 @@ struct Arith<double> {
   static __device__ __forceinline__ double delta(double a) { return 1.0 / (1.0 + exp(a)); }
   static __device__ __forceinline__ double oplus(double p, double d) { return fma(d, fma(-2.0, p, 1.0), p); }
   static __device__ __forceinline__ double mag(double D) { return log((1.0 - D) / D); }
-  static __device__ __forceinline__ double clip_abs(double v, double L, double) { return fmin(fabs(v), L); }
-  static __device__ __forceinline__ double clipped_mag(double D, double L, double) {
-    return fmax(fmin(mag(D), L), 0.0);
-  }
+  static __device__ __forceinline__ double clipped_delta(double v, double L, double) { return delta(fmin(fabs(v), L)); }
+  static __device__ __forceinline__ double clipped_mag(double D, double L) { return fmax(fmin(mag(D), L), 0.0); }
 };
 
 // Sign-bit access: sign_word returns a 32-bit word whose top bit is the sign.
@@ -226,13 +228,13 @@ __device__ __forceinline__ M channel_llr(const M* __restrict__ lp, const uint32_
 // so the combination of a row's other edges is the same deg - 1 fold for every
 // edge; its output magnitude is formed once per row.
 template <typename M, int D, bool CHECKED>
-__device__ __forceinline__ M cn_first_mag(int deg, M ymag, M l_max, M inv_l_max) {
-  const M d = Arith<M>::delta(Arith<M>::clip_abs(ymag, l_max, inv_l_max));
+__device__ __forceinline__ M cn_first_mag(int deg, M ymag, M l_max, M d_lmax) {
+  const M d = Arith<M>::clipped_delta(ymag, l_max, d_lmax);
   M P = M(0);
 #pragma unroll
   for (int k = 0; k < D - 1; ++k)
     if (!CHECKED || k + 1 < deg) P = Arith<M>::oplus(P, d);
-  return Arith<M>::clipped_mag(P, l_max, inv_l_max);
+  return Arith<M>::clipped_mag(P, l_max);
 }
 
 // The first-iteration row of BSC inputs (see cn_first_mag): each edge takes the
@@ -241,7 +243,7 @@ __device__ __forceinline__ M cn_first_mag(int deg, M ymag, M l_max, M inv_l_max)
 template <typename M, typename S, int D, bool CHECKED, int POL>
 __device__ __forceinline__ void cn_row_signs(int deg, const int* __restrict__ cols, const uint32_t* __restrict__ ysrc,
                                              M ymag, S* __restrict__ msg, uint32_t par, bool store, M l_max,
-                                             M inv_l_max) {
+                                             M d_lmax) {
   static_assert(D <= 32, "one bit per edge");
   const int lane = threadIdx.x & 31;
   uint32_t bits = 0;
@@ -250,7 +252,7 @@ __device__ __forceinline__ void cn_row_signs(int deg, const int* __restrict__ co
     if (!CHECKED || k < deg) bits |= ((ld_state<POL>(ysrc + __ldg(cols + k)) >> lane) & 1u) << k;
   if (!store) return;
   par ^= uint32_t(__popc(bits) & 1) << 31;
-  const M mag = cn_first_mag<M, D, CHECKED>(deg, ymag, l_max, inv_l_max);
+  const M mag = cn_first_mag<M, D, CHECKED>(deg, ymag, l_max, d_lmax);
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (!CHECKED || k < deg)
@@ -260,7 +262,7 @@ __device__ __forceinline__ void cn_row_signs(int deg, const int* __restrict__ co
 template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL>
 __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, const M* __restrict__ gsrc,
                                        const uint32_t* __restrict__ ysrc, M ymag, S* __restrict__ msg,
-                                       int first_iter, uint32_t par, bool store, M l_max, M inv_l_max,
+                                       int first_iter, uint32_t par, bool store, M l_max, M d_lmax,
                                        int32_t* __restrict__ lacc, float qscale) {
   int col[D];
 #pragma unroll
@@ -268,7 +270,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   M v[D];
   if (ysrc) {
     if constexpr (!FIXED && D <= 32) {
-      cn_row_signs<M, S, D, CHECKED, POL>(deg, cols, ysrc, ymag, msg, par, store, l_max, inv_l_max);
+      cn_row_signs<M, S, D, CHECKED, POL>(deg, cols, ysrc, ymag, msg, par, store, l_max, d_lmax);
       return;
     } else {
       const int lane = threadIdx.x & 31;
@@ -279,7 +281,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
         par ^= sgn[k];
       }
       if (!store) return;
-      const M mag = cn_first_mag<M, D, CHECKED>(deg, ymag, l_max, inv_l_max);
+      const M mag = cn_first_mag<M, D, CHECKED>(deg, ymag, l_max, d_lmax);
 #pragma unroll
       for (int k = 0; k < D; ++k)
         if (!CHECKED || col[k] >= 0) {
@@ -314,7 +316,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   for (int k = 0; k < D; ++k) {
     const uint32_t sx = Bits<M>::sign_word(v[k]);
     par ^= sx;
-    M d = Arith<M>::delta(Arith<M>::clip_abs(v[k], l_max, inv_l_max));
+    M d = Arith<M>::clipped_delta(v[k], l_max, d_lmax);
     if constexpr (CHECKED) d = col[k] >= 0 ? d : M(0);
     v[k] = Bits<M>::with_sign(d, sx & kSign);
     pre[k] = P;
@@ -326,7 +328,7 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
   for (int k = D - 1; k >= 0; --k) {
     if (!CHECKED || col[k] >= 0) {
       const M Dk = Arith<M>::oplus(pre[k], suf);
-      const M mag = Arith<M>::clipped_mag(Dk, l_max, inv_l_max);
+      const M mag = Arith<M>::clipped_mag(Dk, l_max);
       const M nv = Bits<M>::copy_sign(mag, par ^ Bits<M>::sign_word(v[k]));
       st_msg<POL>(msg + k * kMsgStride<S>, Store<S>::narrow(nv));
       if constexpr (FIXED) {
@@ -346,16 +348,16 @@ template <typename M, typename S, int DMAX, bool FIXED, int POL>
 __device__ __forceinline__ void cn_tile_row_src(int deg, const int* __restrict__ cols,
                                                 const M* __restrict__ gsrc, const uint32_t* __restrict__ ysrc,
                                                 M ym, S* __restrict__ msg, int first_iter, uint32_t par,
-                                                bool store, M l_max, M inv_l_max, int32_t* __restrict__ lacc,
+                                                bool store, M l_max, M d_lmax, int32_t* __restrict__ lacc,
                                                 float qscale) {
   if (deg == DMAX)
-    cn_row<M, S, DMAX, FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, inv_l_max,
+    cn_row<M, S, DMAX, FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, d_lmax,
                                        lacc, qscale);
   else if (DMAX > 1 && deg == DMAX - 1)
     cn_row<M, S, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par,
-                                                             store, l_max, inv_l_max, lacc, qscale);
+                                                             store, l_max, d_lmax, lacc, qscale);
   else
-    cn_row<M, S, DMAX, FIXED, true, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, inv_l_max,
+    cn_row<M, S, DMAX, FIXED, true, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, d_lmax,
                                       lacc, qscale);
 }
 
@@ -446,7 +448,7 @@ __device__ __forceinline__ CnView<M, S> cn_view(const DevCode& c, int tile, uint
 
 // Check row p (degree order) of the view's tile, by one warp.
 template <typename M, typename S, int DMAX, bool FIXED, int POL>
-__device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int first_iter, M l_max, M inv_l_max,
+__device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int first_iter, M l_max, M d_lmax,
                                             float qscale) {
   const int lane = threadIdx.x & 31;
   const int base = v.slice_base[p];
@@ -454,7 +456,7 @@ __device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int fi
   const uint32_t par = ((v.zt[p] >> lane) & 1u) << 31;
   const bool store = (v.act >> lane) & 1u;
   cn_tile_row_src<M, S, DMAX, FIXED, POL>(deg, v.slot_col + base, v.gsrc, v.ysrc, v.ym,
-                                          v.msg + int64_t(base) * kMsgStride<S>, first_iter, par, store, l_max, inv_l_max,
+                                          v.msg + int64_t(base) * kMsgStride<S>, first_iter, par, store, l_max, d_lmax,
                                           v.lacc, qscale);
 }
 
@@ -481,10 +483,10 @@ template <typename M, typename S, int DMAX, bool FIXED, int POL>
 __device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, uint32_t act, int first_iter,
                                             S* __restrict__ c2v, const M* __restrict__ lsrc,
                                             const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
-                                            const uint32_t* __restrict__ zt, M l_max, M inv_l_max,
+                                            const uint32_t* __restrict__ zt, M l_max, M d_lmax,
                                             int32_t* __restrict__ lacc, float qscale) {
   const CnView<M, S> v = cn_view<M, S, POL>(c, tile, act, first_iter, c2v, lsrc, yt, ymag, zt, FIXED ? lacc : nullptr);
-  cn_view_row<M, S, DMAX, FIXED, POL>(v, p, first_iter, l_max, inv_l_max, qscale);
+  cn_view_row<M, S, DMAX, FIXED, POL>(v, p, first_iter, l_max, d_lmax, qscale);
 }
 
 // ------------------------------------------------------------- eq. (2)

@@ -458,7 +458,6 @@ int run_multi(const mbp_group* g, int G, int max_iter, const mbp_opts* o, bool h
   hc->early_exit = o->early_exit;
   hc->cond = 0;
   hc->l_max = float(o->l_max * kToInternal);
-  hc->inv_l_max = 1.0f / hc->l_max;  // as the streaming kernels form it
   int32_t* htg = reinterpret_cast<int32_t*>(host.data() + L.tile_group_off);
   for (int i = 0; i < G; ++i)
     for (int t = 0; t < L.n_tiles[i]; ++t) htg[L.tile_base[i] + t] = i;

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(cn_max_threads(DMAX), cn_min_blocks(DMAX)) cn_
   int64_t r = int64_t(blockIdx.x) * wpb + (threadIdx.x >> 5);
   if (r >= total) return;
   const int first_iter = ctl->t == 1;
-  const float l_max = ctl->l_max, inv_l_max = ctl->inv_l_max;
+  const float l_max = ctl->l_max, d_lmax = Arith<float>::delta(l_max);
   int e = locate(pre, n_ent, r), cur = -1;
   int64_t row0 = 0;
   CnView<float, S> v;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(cn_max_threads(DMAX), cn_min_blocks(DMAX)) cn_
                                         static_cast<const float*>(first_iter ? G.st.lp : G.st.lv), G.st.yt,
                                         static_cast<const float*>(G.st.chan_mag), G.st.zt, nullptr);
     }
-    cn_view_row<float, S, DMAX, false, kPolStream>(v, int(r - row0), first_iter, l_max, inv_l_max, 0.f);
+    cn_view_row<float, S, DMAX, false, kPolStream>(v, int(r - row0), first_iter, l_max, d_lmax, 0.f);
   }
 }
 

@@ -53,7 +53,7 @@ struct MultiCtl {
   int32_t cond;        // 1 while another iteration is to run (also the WHILE node's condition)
   int32_t n_all;       // unfinished tiles (entries of the variable-node list)
   int32_t n_ent[kMaxClasses];
-  float l_max, inv_l_max;  // clip in the decoder's internal LLR unit
+  float l_max;  // clip in the decoder's internal LLR unit
 };
 
 // Launch shapes chosen by the autotuner (or the defaults).

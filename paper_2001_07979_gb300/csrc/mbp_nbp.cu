@@ -81,7 +81,7 @@ __global__ void from_tiles_kernel(const float* __restrict__ src, int F, int n, f
 template <int D, bool CHECKED>
 __device__ __forceinline__ void nbp_row_fwd(int deg, const int* __restrict__ cols, const float* __restrict__ gsrc,
                                             const float* __restrict__ cprev, float* __restrict__ cout, uint32_t par,
-                                            float l_max, float inv_l_max, float a, float b) {
+                                            float l_max, float d_lmax, float a, float b) {
   using A = Arith<float>;
   using B = Bits<float>;
   int col[D];
@@ -100,7 +100,7 @@ __device__ __forceinline__ void nbp_row_fwd(int deg, const int* __restrict__ col
   for (int k = 0; k < D; ++k) {
     const uint32_t sx = B::sign_word(v[k]);
     par ^= sx;
-    float d = A::delta(A::clip_abs(v[k], l_max, inv_l_max));
+    float d = A::clipped_delta(v[k], l_max, d_lmax);
     if (CHECKED) d = col[k] >= 0 ? d : 0.f;
     v[k] = B::with_sign(d, sx & kSign);
     pre[k] = P;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void nbp_row_fwd(int deg, const int* __restrict__ col
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
     if (!CHECKED || col[k] >= 0) {
-      const float mag = A::clipped_mag(A::oplus(pre[k], suf), l_max, inv_l_max);
+      const float mag = A::clipped_mag(A::oplus(pre[k], suf), l_max);
       const float nmag = a * fmaxf(mag - b, 0.f);
       __stcs(cout + k * kLanes, B::copy_sign(nmag, par ^ B::sign_word(v[k])));
     }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) nbp_cn_fwd_kernel(const DevCode c, int t,
   const float* gsrc = lsrc + int64_t(tile) * c.n * kLanes + lane;
   const int* cols = c.slot_col + base;
   const uint32_t par = ((zt[int64_t(tile) * c.m_tot + p] >> lane) & 1u) << 31;
-  const float inv = 1.f / l_max;
+  const float inv = Arith<float>::delta(l_max);  // d_lmax
   if (deg == DMAX) nbp_row_fwd<DMAX, false>(deg, cols, gsrc, cprev, cout, par, l_max, inv, a, b);
   else if (DMAX > 1 && deg == DMAX - 1)
     nbp_row_fwd<(DMAX > 1 ? DMAX - 1 : 1), false>(deg, cols, gsrc, cprev, cout, par, l_max, inv, a, b);
@@ -192,7 +192,7 @@ template <int D, bool CHECKED>
 __device__ __forceinline__ void nbp_row_bwd(int deg, const int* __restrict__ cols, const float* __restrict__ gsrc,
                                             const float* __restrict__ cprev, const float* __restrict__ lbar,
                                             float* __restrict__ w, bool has_next, uint32_t par, float l_max,
-                                            float inv_l_max, float a, float b, float& ga, float& gb) {
+                                            float d_lmax, float a, float b, float& ga, float& gb) {
   using A = Arith<float>;
   using B = Bits<float>;
   int col[D];
@@ -222,7 +222,7 @@ __device__ __forceinline__ void nbp_row_bwd(int deg, const int* __restrict__ col
     const uint32_t sx = B::sign_word(v[k]);
     par ^= sx;
     if (fabsf(v[k]) > l_max) clipped_in |= 1u << k;
-    float d = A::delta(A::clip_abs(v[k], l_max, inv_l_max));
+    float d = A::clipped_delta(v[k], l_max, d_lmax);
     if (CHECKED) d = col[k] >= 0 ? d : 0.f;
     v[k] = B::with_sign(d, sx & kSign);
     pre[k] = P;
@@ -238,7 +238,7 @@ __device__ __forceinline__ void nbp_row_bwd(int deg, const int* __restrict__ col
     if (!CHECKED || col[k] >= 0) {
       const float Dk = A::oplus(pre[k], suf);
       const float g = A::mag(Dk);
-      const float cm = A::clipped_mag(Dk, l_max, inv_l_max);
+      const float cm = A::clipped_mag(Dk, l_max);
       const float s = ((par ^ B::sign_word(v[k])) & kSign) ? -1.f : 1.f;
       if (cm > b) {
         ga += cb[k] * s * (cm - b);
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) nbp_cn_bwd_kernel(const DevCode c, int t,
     const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
     const int* cols = c.slot_col + base;
     const uint32_t par = ((zt[int64_t(tile) * c.m_tot + p] >> lane) & 1u) << 31;
-    const float inv = 1.f / l_max;
+    const float inv = Arith<float>::delta(l_max);  // d_lmax
     if (deg == DMAX)
       nbp_row_bwd<DMAX, false>(deg, cols, lsrc + node0, cprev, lbar + node0, w, has_next, par, l_max, inv, a, b, ga,
                                gb);

@@ -12,6 +12,8 @@
 // writes only the halves of its live frames.
 #pragma once
 
+#include <type_traits>
+
 #include "mbp_device.cuh"
 
 namespace mbp {
@@ -23,16 +25,46 @@ struct Pair;
 template <>
 struct Pair<__half> {
   using T = __half2;
-  static __device__ __forceinline__ float2 widen(T v) { return __half22float2(v); }
   static __device__ __forceinline__ T narrow(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
 template <>
 struct Pair<__nv_bfloat16> {
   using T = __nv_bfloat162;
-  static __device__ __forceinline__ float2 widen(T v) { return __bfloat1622float2(v); }
   static __device__ __forceinline__ T narrow(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
+
+// The word of both tiles' message of an edge (low half: tile 2q).
+template <typename S>
+__device__ __forceinline__ uint32_t ld_pair(const typename Pair<S>::T* p) {
+  return __ldcs(reinterpret_cast<const unsigned int*>(p));
+}
+
+// s0 += lo(w), s1 += hi(w), and v0 -= lo(w), v1 -= hi(w): sm_100's mixed-precision
+// add / fma take the 16-bit operand as is (its widening to FP32 is exact), so each
+// is the FP32 operation on the widened message with one rounding, in one instruction.
+template <typename S>
+__device__ __forceinline__ void add_pair(float& s0, float& s1, uint32_t w) {
+  if constexpr (std::is_same<S, __half>::value)
+    asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; add.rn.f32.f16 %0, l, %0; add.rn.f32.f16 %1, h, %1;}"
+        : "+f"(s0), "+f"(s1) : "r"(w));
+  else
+    asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; add.rn.f32.bf16 %0, l, %0; add.rn.f32.bf16 %1, h, %1;}"
+        : "+f"(s0), "+f"(s1) : "r"(w));
+}
+
+template <typename S>
+__device__ __forceinline__ void sub_pair(float& v0, float& v1, uint32_t w) {
+  if constexpr (std::is_same<S, __half>::value) {
+    const unsigned short m1 = 0xBC00u;  // -1 in FP16
+    asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; fma.rn.f32.f16 %0, l, %3, %0; fma.rn.f32.f16 %1, h, %3, %1;}"
+        : "+f"(v0), "+f"(v1) : "r"(w), "h"(m1));
+  } else {
+    const unsigned short m1 = 0xBF80u;  // -1 in BF16
+    asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; fma.rn.f32.bf16 %0, l, %3, %0; fma.rn.f32.bf16 %1, h, %3, %1;}"
+        : "+f"(v0), "+f"(v1) : "r"(w), "h"(m1));
+  }
+}
 
 // Store a lane's two messages; a retired frame keeps its stored half.
 template <typename S>
@@ -70,7 +102,7 @@ __device__ __forceinline__ PairTiles pair_tiles(int q, int n_tiles, const uint32
 // fold of edges 0 .. k - 1 (padding edges fold as 0).
 template <int D, bool CHECKED>
 __device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre)[D], uint32_t& par, float l_max,
-                                             float inv_l_max) {
+                                             float d_lmax) {
   using A = Arith<float>;
   using B = Bits<float>;
   float P = 0.f;
@@ -78,7 +110,7 @@ __device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre
   for (int k = 0; k < D; ++k) {
     const uint32_t x = B::sign_word(v[k]);
     par ^= x;
-    float d = A::delta(A::clip_abs(v[k], l_max, inv_l_max));
+    float d = A::clipped_delta(v[k], l_max, d_lmax);
     if constexpr (CHECKED) d = k < deg ? d : 0.f;
     v[k] = B::with_sign(d, x & kSign);
     pre[k] = P;
@@ -94,7 +126,7 @@ template <typename S, int D, bool CHECKED>
 __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ cols, const float* __restrict__ g0,
                                             const float* __restrict__ g1, bool h0, bool h1,
                                             typename Pair<S>::T* __restrict__ msg, int first_iter, uint32_t par0,
-                                            uint32_t par1, bool s0, bool s1, float l_max, float inv_l_max) {
+                                            uint32_t par1, bool s0, bool s1, float l_max, float d_lmax) {
   using A = Arith<float>;
   using B = Bits<float>;
   int off[D];
@@ -110,30 +142,26 @@ __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ col
   if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      if (!CHECKED || k < deg) {
-        const float2 o = Pair<S>::widen(__ldcs(msg + k * kLanes));
-        v0[k] -= o.x;
-        v1[k] -= o.y;
-      }
+      if (!CHECKED || k < deg) sub_pair<S>(v0[k], v1[k], ld_pair<S>(msg + k * kLanes));
   }
   if (!s0 && !s1) return;
   // tile 0, then tile 1, sharing the prefix array; tile 0's outputs replace its deltas in v0
   float pre[D];
-  cn_pair_fold<D, CHECKED>(deg, v0, pre, par0, l_max, inv_l_max);
+  cn_pair_fold<D, CHECKED>(deg, v0, pre, par0, l_max, d_lmax);
   float q = 0.f;
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
     const float d = v0[k];
     if (!CHECKED || k < deg)
-      v0[k] = B::copy_sign(A::clipped_mag(A::oplus(pre[k], q), l_max, inv_l_max), par0 ^ B::sign_word(d));
+      v0[k] = B::copy_sign(A::clipped_mag(A::oplus(pre[k], q), l_max), par0 ^ B::sign_word(d));
     q = A::oplus(q, fabsf(d));
   }
-  cn_pair_fold<D, CHECKED>(deg, v1, pre, par1, l_max, inv_l_max);
+  cn_pair_fold<D, CHECKED>(deg, v1, pre, par1, l_max, d_lmax);
   q = 0.f;
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
     if (!CHECKED || k < deg) {
-      const float m1 = A::clipped_mag(A::oplus(pre[k], q), l_max, inv_l_max);
+      const float m1 = A::clipped_mag(A::oplus(pre[k], q), l_max);
       st_pair<S>(msg + k * kLanes, v0[k], B::copy_sign(m1, par1 ^ B::sign_word(v1[k])), s0, s1);
     }
     q = A::oplus(q, fabsf(v1[k]));
@@ -148,7 +176,7 @@ __device__ __forceinline__ void cn_pair_row_signs(int deg, const int* __restrict
                                                   const uint32_t* __restrict__ y0, const uint32_t* __restrict__ y1,
                                                   bool h0, bool h1, float ym0, float ym1,
                                                   typename Pair<S>::T* __restrict__ msg, uint32_t par0,
-                                                  uint32_t par1, bool s0, bool s1, float l_max, float inv_l_max) {
+                                                  uint32_t par1, bool s0, bool s1, float l_max, float d_lmax) {
   static_assert(D <= 32, "one bit per edge");
   const int lane = threadIdx.x & 31;
   uint32_t b0 = 0, b1 = 0;
@@ -162,8 +190,8 @@ __device__ __forceinline__ void cn_pair_row_signs(int deg, const int* __restrict
   if (!s0 && !s1) return;
   par0 ^= uint32_t(__popc(b0) & 1) << 31;
   par1 ^= uint32_t(__popc(b1) & 1) << 31;
-  const float m0 = cn_first_mag<float, D, CHECKED>(deg, ym0, l_max, inv_l_max);
-  const float m1 = cn_first_mag<float, D, CHECKED>(deg, ym1, l_max, inv_l_max);
+  const float m0 = cn_first_mag<float, D, CHECKED>(deg, ym0, l_max, d_lmax);
+  const float m1 = cn_first_mag<float, D, CHECKED>(deg, ym1, l_max, d_lmax);
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (!CHECKED || k < deg)
@@ -197,7 +225,7 @@ __global__ void __launch_bounds__(256, cn_pair_min_blocks(DMAX))
   const float* g0 = lsrc + int64_t(t.t0) * c.n * kLanes + lane;
   const float* g1 = h1 ? lsrc + int64_t(t.t1) * c.n * kLanes + lane : g0;
   const int* cols = c.slot_col + base;
-  const float inv = 1.0f / l_max;
+  const float inv = Arith<float>::delta(l_max);  // d_lmax
   if (deg == DMAX)
     cn_pair_row<S, DMAX, false>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv);
   else if (DMAX > 1 && deg == DMAX - 1)
@@ -232,7 +260,7 @@ __global__ void __launch_bounds__(256) cn_first_pair_kernel(const DevCode c, int
   const uint32_t* y0 = yt + int64_t(t.t0) * c.n;
   const uint32_t* y1 = h1 ? yt + int64_t(t.t1) * c.n : y0;
   const int* cols = c.slot_col + base;
-  const float inv = 1.0f / l_max;
+  const float inv = Arith<float>::delta(l_max);  // d_lmax
   if (deg == DMAX)
     cn_pair_row_signs<S, DMAX, false>(deg, cols, y0, y1, h0, h1, ym0, ym1, msg, par0, par1, t.s0, t.s1, l_max, inv);
   else
@@ -264,14 +292,14 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
   int col[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) col[j] = j < cnt ? __ldg(c.vnode + first + qq + j) : 0;
-  T g[N][D];
+  uint32_t g[N][D];
 #pragma unroll
   for (int j = 0; j < N; ++j)
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const bool on = j < cnt && k < d;
       const int slot = on ? __ldg(slots0 + j * d + k) : 0;
-      g[j][k] = on ? __ldcs(msg + int64_t(slot) * kLanes) : Pair<S>::narrow(0.f, 0.f);
+      g[j][k] = on ? ld_pair<S>(msg + int64_t(slot) * kLanes) : 0u;
     }
   const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
   const float ym0 = yt && h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
@@ -290,11 +318,7 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
     }
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      if (k < d) {
-        const float2 w = Pair<S>::widen(g[j][k]);
-        sum0 += w.x;
-        sum1 += w.y;
-      }
+      if (k < d) add_pair<S>(sum0, sum1, g[j][k]);
     if (h0) {
       if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
       const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
   unsigned gen = 0;
   const int warps = gridDim.x * (blockDim.x >> 5);
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const M inv_l_max = M(1) / l_max;
+  const M d_lmax = Arith<M>::delta(l_max);
   const int row_groups = (c.m_tot + 31) / 32;
   __shared__ int last_block;
 
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
         const uint32_t act = __ldcg(active + tile);
         if (act)
           cn_tile_row<M, M, DMAX, false, kPolCoherent>(c, tile, it % c.m_tot, act, t == 1, c2v, lsrc, yt, ymag, zt,
-                                                    l_max, inv_l_max, nullptr, 0.f);
+                                                    l_max, d_lmax, nullptr, 0.f);
       }
       if (!grid_sync(ctl, gen, bc)) return;
       for (int it = gw; it < gt * c.n; it += warps) {

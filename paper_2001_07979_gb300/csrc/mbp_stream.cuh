@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256, cn_min_blocks<M>(DMAX)) cn_kernel(const D
   const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
   if (p >= p1) return;
   cn_tile_row<M, S, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, yt, ymag, zt, l_max,
-                                          M(1) / l_max, lacc, qscale);
+                                          Arith<M>::delta(l_max), lacc, qscale);
 }
 
 // Iteration 1 of BSC inputs in a kernel of its own (sign words in, messages
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) cn_first_kernel(const DevCode c, int p0, 
   const M ym = __ldg(ymag + tile * kLanes + lane);
   S* msg = c2v + msg_at<S>(tile, c.s_tot, lane) + int64_t(base) * kMsgStride<S>;
   const uint32_t* ysrc = yt + int64_t(tile) * c.n;
-  const M inv = M(1) / l_max;
+  const M inv = Arith<M>::delta(l_max);  // d_lmax
   if (deg == DMAX) cn_row_signs<M, S, DMAX, false, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
   else cn_row_signs<M, S, DMAX, true, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
 }

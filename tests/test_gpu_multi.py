@@ -265,13 +265,18 @@ def test_uneven_batch_recipe_small(mbp):
     assert ok >= 200
 
 
-def test_set_tuning_selects_kernels_without_changing_results(mbp, batch):
-    ref = mbp.mbp_decode_multi([g.arg() for g in batch], 30, want_soft=True)
+@pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
+def test_set_tuning_selects_kernels_without_changing_results(mbp, batch, msg):
+    """Persistent list kernels (one tile per warp) and grid kernels (for FP16/BF16 the tile-pair kernels, two
+    frames per lane, mixed-precision adds) are separate implementations of the same per-frame arithmetic:
+    equal outputs, bit for bit."""
+    dt = {"f32": mbp.MSG_F32, "f16": mbp.MSG_F16, "bf16": mbp.MSG_BF16}[msg]
+    ref = mbp.mbp_decode_multi([g.arg() for g in batch], 30, want_soft=True, msg_dtype=dt)
     torch.cuda.synchronize()
     for tu in (dict(grid_kernels=0, cn_warps=2, cn_waves=2, vn_warps=4, syn_warps=8),
                dict(grid_kernels=1, cn_warps=8, cn_waves=1, vn_warps=8, syn_warps=8)):
-        mbp.mbp_multi_set_tuning([g.arg() for g in batch], tu)
-        out = mbp.mbp_decode_multi([g.arg() for g in batch], 30, want_soft=True)
+        mbp.mbp_multi_set_tuning([g.arg() for g in batch], tu, msg_dtype=dt)
+        out = mbp.mbp_decode_multi([g.arg() for g in batch], 30, want_soft=True, msg_dtype=dt)
         torch.cuda.synchronize()
         for a, b in zip(ref, out):
             for k in ("x_hat_bits", "iters", "success", "soft"):
