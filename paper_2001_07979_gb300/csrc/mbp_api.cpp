@@ -331,7 +331,11 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   }
   // variable nodes by degree class, each with a dense table of its slots (the variable-node kernel then
   // loads a node and its slots together)
-  std::vector<int32_t> vnode(n), vslot(std::max<int64_t>(e_tot, 1));
+  std::vector<int32_t> vnode(n), vslot(std::max<int64_t>(e_tot, 1)), vrow(std::max<int64_t>(e_tot, 1));
+  std::vector<int32_t> slot_row(std::max<int64_t>(d.s_tot, 1));
+  for (int64_t p = 0; p < m_tot; ++p)  // row position << 6 | degree - 1 (degree <= kMaxRowDeg = 64)
+    for (int32_t q = slice_base[p]; q < slice_base[p + 1]; ++q)
+      slot_row[q] = int32_t(p << 6) | (slice_base[p + 1] - slice_base[p] - 1);
   for (int32_t i = 0; i < n; ++i) vnode[i] = i;
   std::stable_sort(vnode.begin(), vnode.end(), [&](int32_t a, int32_t b) {
     return col_ptr[a + 1] - col_ptr[a] < col_ptr[b + 1] - col_ptr[b];
@@ -349,7 +353,10 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
         d.vclass_toff[d.n_vclass] = t;
         ++d.n_vclass;
       }
-      for (int32_t a = col_ptr[i]; a < col_ptr[i + 1]; ++a) vslot[t++] = col_slot[a];
+      for (int32_t a = col_ptr[i]; a < col_ptr[i + 1]; ++a) {
+        vslot[t] = col_slot[a];
+        vrow[t++] = slot_row[col_slot[a]];
+      }
     }
     if (fits) d.vclass_first[d.n_vclass] = n;
     else d.n_vclass = 0;
@@ -363,7 +370,7 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
       {row_ptr.data(), row_ptr.size() * 4, 0},       {col_idx.data(), col_idx.size() * 4, 0},
       {edge_slot.data(), edge_slot.size() * 4, 0},   {perm_mat.data(), perm_mat.size(), 0},
       {perm_local.data(), perm_local.size() * 4, 0}, {vnode.data(), vnode.size() * 4, 0},
-      {vslot.data(), vslot.size() * 4, 0}};
+      {vslot.data(), vslot.size() * 4, 0},           {vrow.data(), vrow.size() * 4, 0}};
   size_t total = 0;
   for (auto& p : parts) {
     p.off = total;
@@ -400,6 +407,8 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   d.row_local = reinterpret_cast<const int32_t*>(base + parts[8].off);
   d.vnode = reinterpret_cast<const int32_t*>(base + parts[9].off);
   d.vslot = reinterpret_cast<const int32_t*>(base + parts[10].off);
+  // the packed row table holds positions below 2^25; larger codes keep iteration 1 per edge
+  d.vrow = m_tot < (int64_t(1) << 25) ? reinterpret_cast<const int32_t*>(base + parts[11].off) : nullptr;
   h->d = d;
   *out = h;
   return MBP_OK;

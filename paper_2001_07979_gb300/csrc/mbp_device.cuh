@@ -237,6 +237,30 @@ __device__ __forceinline__ M cn_first_mag(int deg, M ymag, M l_max, M d_lmax) {
   return Arith<M>::clipped_mag(P, l_max);
 }
 
+// cn_first_mag for a row of any degree (the same operations in the same order).
+template <typename M>
+__device__ __forceinline__ M cn_first_mag_any(int deg, M ymag, M l_max, M d_lmax) {
+  const M d = Arith<M>::clipped_delta(ymag, l_max, d_lmax);
+  M P = M(0);
+  for (int k = 0; k + 1 < deg; ++k) P = Arith<M>::oplus(P, d);
+  return Arith<M>::clipped_mag(P, l_max);
+}
+
+// The stored value of a first-iteration magnitude in row form: rounded to the
+// message type, so that a message rebuilt from it equals the stored one.
+template <typename M, typename S>
+__device__ __forceinline__ M row_mag(M mag) {
+  return M(Store<S>::widen(Store<S>::narrow(mag)));
+}
+
+// A first-iteration C2V in row form (DevState::fmag): the magnitude of its row's
+// degree with sign bit `lane` of rs ^ y (rs the row's sign word, y the node's
+// sign word).
+template <typename M>
+__device__ __forceinline__ M row_msg(M rm, uint32_t rs, uint32_t y, int lane) {
+  return Bits<M>::copy_sign(rm, (rs ^ y) << (31 - lane));
+}
+
 // The first-iteration row of BSC inputs (see cn_first_mag): each edge takes the
 // shared magnitude with the sign of the other edges' bits and z_j. The row's
 // bits are kept as one mask (D <= 32), edges k >= deg are padding.
@@ -259,11 +283,12 @@ __device__ __forceinline__ void cn_row_signs(int deg, const int* __restrict__ co
       st_msg<POL>(msg + k * kMsgStride<S>, Store<S>::narrow(Bits<M>::copy_sign(mag, par ^ (((bits >> k) & 1u) << 31))));
 }
 
-template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL>
+template <typename M, typename S, int D, bool FIXED, bool CHECKED, int POL, bool RIN = false>
 __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, const M* __restrict__ gsrc,
                                        const uint32_t* __restrict__ ysrc, M ymag, S* __restrict__ msg,
                                        int first_iter, uint32_t par, bool store, M l_max, M d_lmax,
-                                       int32_t* __restrict__ lacc, float qscale) {
+                                       int32_t* __restrict__ lacc, float qscale, const M* __restrict__ rm_p,
+                                       const uint32_t* __restrict__ rs_p, const uint32_t* __restrict__ yprev) {
   int col[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : -1;
@@ -299,7 +324,19 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
     for (int k = 0; k < D; ++k) v[k] = (!CHECKED || col[k] >= 0) ? ld_state<POL>(gsrc + col[k] * kLanes) : M(0);
   }
   [[maybe_unused]] M old[FIXED ? D : 1];
-  if (!first_iter) {
+  if constexpr (RIN) {  // iteration 2 after a row-form iteration 1: C2V^1 rebuilt from the row
+    const int lane = threadIdx.x & 31;
+    const M rm = ld_state<POL>(rm_p);
+    const uint32_t rs = ld_state<POL>(rs_p);
+    // lane k fetches edge k's sign word (one gather for the row; rows of up to 32
+    // edges), then each edge's word is broadcast
+    const uint32_t ymine = lane < deg ? ld_state<POL>(yprev + __ldg(cols + lane)) : 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const uint32_t yk = __shfl_sync(kFull, ymine, k & 31);
+      if (!CHECKED || col[k] >= 0) v[k] -= row_msg(rm, rs, yk, lane);
+    }
+  } else if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const M o = (!CHECKED || col[k] >= 0) ? M(Store<S>::widen(ld_msg<POL>(msg + k * kMsgStride<S>))) : M(0);
@@ -344,21 +381,26 @@ __device__ __forceinline__ void cn_row(int deg, const int* __restrict__ cols, co
 // DMAX - 1 edges take an unchecked body. lsrc is the posterior (L_P in the
 // first iteration of general inputs); the first iteration of BSC inputs reads
 // the sign words yt and magnitudes ymag instead.
-template <typename M, typename S, int DMAX, bool FIXED, int POL>
+// RIN: the old messages are the row's first-iteration messages in row form
+// (iteration 2): rm_p / rs_p / yprev.
+template <typename M, typename S, int DMAX, bool FIXED, int POL, bool RIN = false>
 __device__ __forceinline__ void cn_tile_row_src(int deg, const int* __restrict__ cols,
                                                 const M* __restrict__ gsrc, const uint32_t* __restrict__ ysrc,
                                                 M ym, S* __restrict__ msg, int first_iter, uint32_t par,
                                                 bool store, M l_max, M d_lmax, int32_t* __restrict__ lacc,
-                                                float qscale) {
+                                                float qscale, const M* __restrict__ rm_p = nullptr,
+                                                const uint32_t* __restrict__ rs_p = nullptr,
+                                                const uint32_t* __restrict__ yprev = nullptr) {
   if (deg == DMAX)
-    cn_row<M, S, DMAX, FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, d_lmax,
-                                       lacc, qscale);
+    cn_row<M, S, DMAX, FIXED, false, POL, RIN>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, d_lmax,
+                                            lacc, qscale, rm_p, rs_p, yprev);
   else if (DMAX > 1 && deg == DMAX - 1)
-    cn_row<M, S, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par,
-                                                             store, l_max, d_lmax, lacc, qscale);
+    cn_row<M, S, (DMAX > 1 ? DMAX - 1 : 1), FIXED, false, POL, RIN>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par,
+                                                                  store, l_max, d_lmax, lacc, qscale, rm_p, rs_p,
+                                                                  yprev);
   else
-    cn_row<M, S, DMAX, FIXED, true, POL>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, d_lmax,
-                                      lacc, qscale);
+    cn_row<M, S, DMAX, FIXED, true, POL, RIN>(deg, cols, gsrc, ysrc, ym, msg, first_iter, par, store, l_max, d_lmax,
+                                           lacc, qscale, rm_p, rs_p, yprev);
 }
 
 // The min-sum check rule (an algorithm variant) for one row and one lane, FP32
@@ -423,6 +465,11 @@ struct CnView {
   const uint32_t* zt;    // the tile's syndrome words
   int32_t* lacc;         // the tile's fixed-point sums, lane (FIXED) or NULL
   uint32_t act;          // lanes still decoding
+  // iteration 2 after a row-form iteration 1 (else NULL): the tile's magnitude table (by row degree, lane),
+  // row sign words and Bob's sign words
+  const M* rm;
+  const uint32_t* rs;
+  const uint32_t* yprev;
 };
 
 template <typename M, typename S, int POL>
@@ -443,11 +490,14 @@ __device__ __forceinline__ CnView<M, S> cn_view(const DevCode& c, int tile, uint
   v.zt = zt + int64_t(tile) * c.m_tot;
   v.lacc = lacc ? lacc + node0 : nullptr;
   v.act = act;
+  v.rm = nullptr;
+  v.rs = nullptr;
+  v.yprev = nullptr;
   return v;
 }
 
 // Check row p (degree order) of the view's tile, by one warp.
-template <typename M, typename S, int DMAX, bool FIXED, int POL>
+template <typename M, typename S, int DMAX, bool FIXED, int POL, bool RIN = false>
 __device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int first_iter, M l_max, M d_lmax,
                                             float qscale) {
   const int lane = threadIdx.x & 31;
@@ -455,9 +505,10 @@ __device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int fi
   const int deg = v.slice_base[p + 1] - base;
   const uint32_t par = ((v.zt[p] >> lane) & 1u) << 31;
   const bool store = (v.act >> lane) & 1u;
-  cn_tile_row_src<M, S, DMAX, FIXED, POL>(deg, v.slot_col + base, v.gsrc, v.ysrc, v.ym,
-                                          v.msg + int64_t(base) * kMsgStride<S>, first_iter, par, store, l_max, d_lmax,
-                                          v.lacc, qscale);
+  cn_tile_row_src<M, S, DMAX, FIXED, POL, RIN>(deg, v.slot_col + base, v.gsrc, v.ysrc, v.ym,
+                                               v.msg + int64_t(base) * kMsgStride<S>, first_iter, par, store, l_max,
+                                               d_lmax, v.lacc, qscale, RIN ? v.rm + (deg - 1) * kLanes : nullptr,
+                                               RIN ? v.rs + p : nullptr, v.yprev);
 }
 
 // Min-sum rule for check row p of the view's tile (FP32 arithmetic).

@@ -72,6 +72,7 @@ struct DevCode {
   int64_t vclass_toff[kMaxVClasses];
   const int32_t* vnode;       // [n]
   const int32_t* vslot;       // [e_tot]
+  const int32_t* vrow;        // [e_tot] each vslot entry's row: position << 6 | degree - 1
 };
 
 // Per-call decoder state carved out of the caller's workspace.
@@ -89,6 +90,11 @@ struct DevState {
   uint32_t* fail;     // [n_tiles][u] lanes whose hard decision violates some check of H_l
   int32_t* counters;  // [4]: unfinished tiles, non-finite flag
   void* ctl;          // control block of the resident schedule (barrier, retirement)
+  // Row form of the first iteration's messages (BSC inputs): the C2V of row p
+  // (degree d) to a node is +-fmag[tile][d - 1][lane], with sign bit lane of
+  // rsgn[tile][p] ^ yt[tile][node]
+  void* fmag;         // [n_tiles][kMaxRowDeg][kLanes] arithmetic type (rounded to the message type)
+  uint32_t* rsgn;     // [n_tiles][m_tot]
   // staging for mbp_decode_bsc_host
   uint32_t* io_y;
   double* io_qber;
@@ -160,7 +166,7 @@ int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool 
                       float inv_qscale, cudaStream_t s);
 // one flooding iteration of one group, no host synchronisation (grouped decode; float arithmetic)
 template <typename M, typename S>
-cudaError_t stream_group_step(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s);
+cudaError_t stream_group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s);
 template <typename M>
 int resident_group(const DevCode& c, int n_tiles);
 template <typename M>

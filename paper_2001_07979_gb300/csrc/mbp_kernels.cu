@@ -197,13 +197,31 @@ __global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv
   out[idx] = M(v * Arith<M>::kToLLR);
 }
 
+// One frame's C2V per stacked CSR edge; when the decode stopped after a
+// row-form iteration 1 (flag counters[2]), rebuilt from the rows (row_msg).
 template <typename M, typename S>
-__global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, int frame, M* __restrict__ out) {
+__global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, int frame, M* __restrict__ out,
+                                  const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn,
+                                  const uint32_t* __restrict__ yt, const int32_t* __restrict__ counters) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= c.e_tot) return;
   const int tile = frame / kLanes, lane = frame % kLanes;
-  out[e] = M(Store<S>::widen(c2v[msg_at<S>(tile, c.s_tot, lane) + int64_t(c.edge_slot[e]) * kMsgStride<S>])) *
-           Arith<M>::kToLLR;
+  const int slot = c.edge_slot[e];
+  M v;
+  if (counters[2]) {
+    int lo = 0, hi = c.m_tot;  // the row position p with slice_base[p] <= slot < slice_base[p + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (c.slice_base[mid] <= slot) lo = mid;
+      else hi = mid;
+    }
+    const int deg = c.slice_base[lo + 1] - c.slice_base[lo];
+    v = row_msg(fmag[(int64_t(tile) * kMaxRowDeg + deg - 1) * kLanes + lane], rsgn[int64_t(tile) * c.m_tot + lo],
+                yt[int64_t(tile) * c.n + c.col_idx[e]], lane);
+  } else {
+    v = M(Store<S>::widen(c2v[msg_at<S>(tile, c.s_tot, lane) + int64_t(slot) * kMsgStride<S>]));
+  }
+  out[e] = v * Arith<M>::kToLLR;
 }
 
 // ------------------------------------------------------------- driver
@@ -311,7 +329,7 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
 #undef CK
 }
 
-constexpr int kRegions = 18;
+constexpr int kRegions = 20;
 
 // bytes of one stored message and of one posterior / channel value
 size_t msg_size(int msg_dtype) {
@@ -346,6 +364,8 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
       host_io ? size_t(F) * 4 : 0,                                    // io_iters
       host_io ? size_t(F) : 0,                                        // io_success
       NT * size_t(c.n) * 4,                                           // yt
+      NT * size_t(kMaxRowDeg) * kLanes * node_size(msg_dtype),        // fmag
+      NT * size_t(c.m_tot) * 4,                                       // rsgn
   };
   size_t t = 0;
   for (int i = 0; i < kRegions; ++i) {
@@ -400,6 +420,8 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->fail = reinterpret_cast<uint32_t*>(b + o[7]);
   st->chan_mag = b + o[8];
   st->yt = reinterpret_cast<uint32_t*>(b + o[17]);
+  st->fmag = b + o[18];
+  st->rsgn = reinterpret_cast<uint32_t*>(b + o[19]);
   st->counters = reinterpret_cast<int32_t*>(b + o[9]);
   st->ctl = b + o[10];
   st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;
@@ -455,18 +477,14 @@ cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtyp
                               cudaStream_t s) {
   if (c.e_tot == 0) return cudaSuccess;
   const unsigned grid = blocks_for(c.e_tot, 256);
-  if (msg_dtype == MBP_MSG_F64)
-    export_c2v_kernel<double, double><<<grid, 256, 0, s>>>(c, static_cast<const double*>(st.c2v), frame,
-                                                            static_cast<double*>(out));
-  else if (msg_dtype == MBP_MSG_F16)
-    export_c2v_kernel<float, __half><<<grid, 256, 0, s>>>(c, static_cast<const __half*>(st.c2v), frame,
-                                                           static_cast<float*>(out));
-  else if (msg_dtype == MBP_MSG_BF16)
-    export_c2v_kernel<float, __nv_bfloat16><<<grid, 256, 0, s>>>(c, static_cast<const __nv_bfloat16*>(st.c2v), frame,
-                                                                  static_cast<float*>(out));
-  else
-    export_c2v_kernel<float, float><<<grid, 256, 0, s>>>(c, static_cast<const float*>(st.c2v), frame,
-                                                          static_cast<float*>(out));
+#define MBP_EXPORT(M, S)                                                                                     \
+  export_c2v_kernel<M, S><<<grid, 256, 0, s>>>(c, static_cast<const S*>(st.c2v), frame, static_cast<M*>(out), \
+                                               static_cast<const M*>(st.fmag), st.rsgn, st.yt, st.counters)
+  if (msg_dtype == MBP_MSG_F64) MBP_EXPORT(double, double);
+  else if (msg_dtype == MBP_MSG_F16) MBP_EXPORT(float, __half);
+  else if (msg_dtype == MBP_MSG_BF16) MBP_EXPORT(float, __nv_bfloat16);
+  else MBP_EXPORT(float, float);
+#undef MBP_EXPORT
   return cudaGetLastError();
 }
 

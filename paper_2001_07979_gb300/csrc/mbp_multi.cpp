@@ -147,14 +147,15 @@ cudaError_t issue_prologue(const Kernels& k, const MultiTables& tb, const MultiS
 }
 
 // One iteration's decoding work: eq. (6) per class, eq. (2), the stopping test per class (persistent kernels);
-// or every group's streaming-schedule kernels (grid kernels, first_iter fixed at capture).
+// or every group's streaming-schedule kernels (grid kernels; iter = 1, 2 or 0 for a later iteration, fixed at
+// capture: iteration 1 may leave its messages in row form, which iteration 2 reads).
 cudaError_t issue_work(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu,
-                       int sms, const Groups& gs, int first_iter, cudaStream_t s) {
+                       int sms, const Groups& gs, int iter, cudaStream_t s) {
   cudaError_t e;
   if (tu.grid) {
     for (size_t g = 0; g < gs.code.size(); ++g) {
       if (gs.st[g].F == 0) continue;
-      if ((e = k.group_step(gs.code[g], gs.st[g], first_iter, gs.l_max, s)) != cudaSuccess) return e;
+      if ((e = k.group_step(gs.code[g], gs.st[g], iter, gs.l_max, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
@@ -183,7 +184,7 @@ cudaError_t issue_retire(const Kernels& k, const MultiTables& tb, const MultiSha
 
 // Grid kernels: one IF node per group with frames (parallel branches, each running its group's step while the
 // group has unfinished tiles), all depending on `deps`; returns the IF nodes.
-int add_group_branches(const Kernels& k, const Groups& gs, const GroupConds& gc, int first_iter, cudaGraph_t graph,
+int add_group_branches(const Kernels& k, const Groups& gs, const GroupConds& gc, int iter, cudaGraph_t graph,
                        const std::vector<cudaGraphNode_t>& deps, cudaStream_t cs,
                        std::vector<cudaGraphNode_t>* nodes) {
   cudaError_t e;
@@ -200,7 +201,7 @@ int add_group_branches(const Kernels& k, const Groups& gs, const GroupConds& gc,
     if ((e = cudaStreamBeginCaptureToGraph(cs, sub, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
         cudaSuccess)
       return cuda_error(e, "begin capture (group step)");
-    const cudaError_t ke = k.group_step(gs.code[g], gs.st[g], first_iter, gs.l_max, cs);
+    const cudaError_t ke = k.group_step(gs.code[g], gs.st[g], iter, gs.l_max, cs);
     cudaGraph_t out = sub;
     const cudaError_t ee = cudaStreamEndCapture(cs, &out);
     if (ke != cudaSuccess) return cuda_error(ke, "group step during capture");
@@ -233,8 +234,8 @@ int capture_after(cudaGraph_t graph, const std::vector<cudaGraphNode_t>& deps, c
 }
 
 // The whole loop as one graph. Persistent kernels: the prologue, then a WHILE node whose body is one
-// iteration. Grid kernels: the prologue, iteration 1, then WHILE{iteration}, where each iteration is one IF
-// node per group (its step runs only while the group has unfinished tiles; the groups run as parallel
+// iteration. Grid kernels: the prologue, iterations 1 and 2, then WHILE{iteration}, where each iteration is
+// one IF node per group (its step runs only while the group has unfinished tiles; the groups run as parallel
 // branches) followed by the retire kernel, which sets the WHILE and IF conditions for the next iteration.
 int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu, int sms,
                 const Groups& gs, cudaGraphExec_t* out) {
@@ -242,7 +243,7 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
   cudaStream_t cs = nullptr;
   cudaGraph_t g = nullptr;
   int rc = MBP_OK;
-  GroupConds ga{0, {}}, gb{0, {}};  // IF conditions of iteration 1 and of the loop body
+  GroupConds ga{0, {}}, g2{0, {}}, gb{0, {}};  // IF conditions of iterations 1, 2 and of the loop body
   std::vector<cudaGraphNode_t> leaf, branches;
 #define GK(call, what)                 \
   if ((e = (call)) != cudaSuccess) {   \
@@ -257,22 +258,28 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
     cudaGraphConditionalHandle h;
     GK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault), "cudaGraphConditionalHandleCreate");
     if (tu.grid) {
-      ga.n = gb.n = int(gs.code.size());
+      ga.n = g2.n = gb.n = int(gs.code.size());
       for (size_t q = 0; q < gs.code.size(); ++q) {
-        ga.h[q] = gb.h[q] = ~0ull;
+        ga.h[q] = g2.h[q] = gb.h[q] = ~0ull;
         if (gs.st[q].F == 0) continue;
-        cudaGraphConditionalHandle ha, hb;
+        cudaGraphConditionalHandle ha, h2, hb;
         GK(cudaGraphConditionalHandleCreate(&ha, g, 1, cudaGraphCondAssignDefault), "conditional handle (IF)");
+        GK(cudaGraphConditionalHandleCreate(&h2, g, 1, cudaGraphCondAssignDefault), "conditional handle (IF)");
         GK(cudaGraphConditionalHandleCreate(&hb, g, 1, cudaGraphCondAssignDefault), "conditional handle (IF)");
         ga.h[q] = ha;
+        g2.h[q] = h2;
         gb.h[q] = hb;
       }
     }
     GR(capture_after(g, {}, cs, [&](cudaStream_t st) { return issue_prologue(k, tb, sh, tu, sms, 1, h, ga, st); },
                      &leaf, "capture (prologue)"));
-    if (tu.grid) {  // iteration 1
+    if (tu.grid) {  // iterations 1 and 2
       branches.clear();
       GR(add_group_branches(k, gs, ga, 1, g, leaf, cs, &branches));
+      GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, g2, st); },
+                       &leaf, "capture (retire)"));
+      branches.clear();
+      GR(add_group_branches(k, gs, g2, 2, g, leaf, cs, &branches));
       GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, gb, st); },
                        &leaf, "capture (retire)"));
     }
@@ -495,7 +502,7 @@ int run_multi(const mbp_group* g, int G, int max_iter, const mbp_opts* o, bool h
         return cuda_error(e, "read loop condition");
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
       if (!cond) break;
-      if ((e = issue_work(k, tb, sh, tu, sms, gs, t == 1, s)) != cudaSuccess) return cuda_error(e, "grouped iteration");
+      if ((e = issue_work(k, tb, sh, tu, sms, gs, t <= 2 ? t : 0, s)) != cudaSuccess) return cuda_error(e, "grouped iteration");
       if ((e = issue_retire(k, tb, sh, tu, 0, 0, kNoConds, s)) != cudaSuccess) return cuda_error(e, "grouped retire");
     }
   } else {

@@ -122,24 +122,48 @@ __device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre
 // first iteration of general inputs), prefix / suffix (+) folds per frame,
 // output magnitude and sign as in cn_row. g0 / g1 are the tiles' posteriors at
 // this lane; h0 / h1 say whether a tile has live frames (warp-uniform).
+// rp != NULL (iteration 2 after a row-form iteration 1): the old messages are
+// rebuilt from the tiles' row magnitudes rp->m (this lane) and sign words rp->s
+// and Bob's sign words rp->y (row_msg), as the stored ones would read.
+struct PairRows {
+  float m0, m1;
+  uint32_t s0, s1;
+  const uint32_t* y0;
+  const uint32_t* y1;
+};
+
 template <typename S, int D, bool CHECKED>
 __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ cols, const float* __restrict__ g0,
                                             const float* __restrict__ g1, bool h0, bool h1,
                                             typename Pair<S>::T* __restrict__ msg, int first_iter, uint32_t par0,
-                                            uint32_t par1, bool s0, bool s1, float l_max, float d_lmax) {
+                                            uint32_t par1, bool s0, bool s1, float l_max, float d_lmax,
+                                            const PairRows* rp) {
   using A = Arith<float>;
   using B = Bits<float>;
-  int off[D];
+  int col[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) off[k] = (!CHECKED || k < deg) ? __ldg(cols + k) * kLanes : 0;
+  for (int k = 0; k < D; ++k) col[k] = (!CHECKED || k < deg) ? __ldg(cols + k) : 0;
   float v0[D], v1[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const bool on = !CHECKED || k < deg;
-    v0[k] = on && h0 ? __ldg(g0 + off[k]) : 0.f;
-    v1[k] = on && h1 ? __ldg(g1 + off[k]) : 0.f;
+    v0[k] = on && h0 ? __ldg(g0 + col[k] * kLanes) : 0.f;
+    v1[k] = on && h1 ? __ldg(g1 + col[k] * kLanes) : 0.f;
   }
-  if (!first_iter) {
+  if (rp) {  // lane k fetches edge k's sign words (two gathers for the row), broadcast per edge
+    const int lane = threadIdx.x & 31;
+    const int mycol = lane < deg ? __ldg(cols + lane) : 0;
+    const uint32_t my0 = lane < deg && h0 ? __ldg(rp->y0 + mycol) : 0u;
+    const uint32_t my1 = lane < deg && h1 ? __ldg(rp->y1 + mycol) : 0u;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const uint32_t y0k = __shfl_sync(kFull, my0, k & 31), y1k = __shfl_sync(kFull, my1, k & 31);
+      if (!CHECKED || k < deg) {
+        if (h0) v0[k] -= row_msg(rp->m0, rp->s0, y0k, lane);
+        if (h1) v1[k] -= row_msg(rp->m1, rp->s1, y1k, lane);
+      }
+    }
+  } else if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k)
       if (!CHECKED || k < deg) sub_pair<S>(v0[k], v1[k], ld_pair<S>(msg + k * kLanes));
@@ -204,12 +228,16 @@ __device__ __forceinline__ void cn_pair_row_signs(int deg, const int* __restrict
 constexpr int cn_pair_min_blocks(int dmax) { return dmax <= 14 ? 4 : (dmax <= 16 ? 3 : 2); }
 
 // One warp per (tile pair, check row): 8 rows per block, pair = blockIdx.y,
-// rows p0 .. p1 - 1.
-template <typename S, int DMAX>
+// rows p0 .. p1 - 1. RIN: iteration 2 after a row-form iteration 1 (fmag, rsgn;
+// the kernel clears the row-form flag counters[2]).
+template <typename S, int DMAX, bool RIN>
 __global__ void __launch_bounds__(256, cn_pair_min_blocks(DMAX))
     cn_pair_kernel(const DevCode c, int p0, int p1, int first_iter, S* __restrict__ c2v,
                    const float* __restrict__ lsrc, const uint32_t* __restrict__ zt,
-                   const uint32_t* __restrict__ active, int n_tiles, float l_max) {
+                   const uint32_t* __restrict__ active, int n_tiles, float l_max, const float* __restrict__ fmag,
+                   const uint32_t* __restrict__ rsgn, const uint32_t* __restrict__ yt,
+                   int32_t* __restrict__ counters) {
+  if (RIN && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[2] = 0;
   const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
   if ((t.a0 | t.a1) == 0) return;
   const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -226,13 +254,24 @@ __global__ void __launch_bounds__(256, cn_pair_min_blocks(DMAX))
   const float* g1 = h1 ? lsrc + int64_t(t.t1) * c.n * kLanes + lane : g0;
   const int* cols = c.slot_col + base;
   const float inv = Arith<float>::delta(l_max);  // d_lmax
+  PairRows rows;
+  if constexpr (RIN) {
+    const int64_t r0 = int64_t(t.t0) * c.m_tot + p, r1 = int64_t(t.t1) * c.m_tot + p;
+    rows.m0 = h0 ? __ldg(fmag + (int64_t(t.t0) * kMaxRowDeg + deg - 1) * kLanes + lane) : 0.f;
+    rows.m1 = h1 ? __ldg(fmag + (int64_t(t.t1) * kMaxRowDeg + deg - 1) * kLanes + lane) : 0.f;
+    rows.s0 = h0 ? __ldg(rsgn + r0) : 0u;
+    rows.s1 = h1 ? __ldg(rsgn + r1) : 0u;
+    rows.y0 = yt + int64_t(t.t0) * c.n;
+    rows.y1 = h1 ? yt + int64_t(t.t1) * c.n : rows.y0;
+  }
+  const PairRows* rp = RIN ? &rows : nullptr;
   if (deg == DMAX)
-    cn_pair_row<S, DMAX, false>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv);
+    cn_pair_row<S, DMAX, false>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv, rp);
   else if (DMAX > 1 && deg == DMAX - 1)
     cn_pair_row<S, (DMAX > 1 ? DMAX - 1 : 1), false>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0,
-                                                     t.s1, l_max, inv);
+                                                     t.s1, l_max, inv, rp);
   else
-    cn_pair_row<S, DMAX, true>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv);
+    cn_pair_row<S, DMAX, true>(deg, cols, g0, g1, h0, h1, msg, first_iter, par0, par1, t.s0, t.s1, l_max, inv, rp);
 }
 
 // Iteration 1 of BSC inputs for a tile pair.
@@ -292,6 +331,7 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
   int col[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) col[j] = j < cnt ? __ldg(c.vnode + first + qq + j) : 0;
+  const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
   uint32_t g[N][D];
 #pragma unroll
   for (int j = 0; j < N; ++j)
@@ -301,7 +341,6 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
       const int slot = on ? __ldg(slots0 + j * d + k) : 0;
       g[j][k] = on ? ld_pair<S>(msg + int64_t(slot) * kLanes) : 0u;
     }
-  const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
   const float ym0 = yt && h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
   const float ym1 = yt && h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
 #pragma unroll
@@ -319,6 +358,74 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
 #pragma unroll
     for (int k = 0; k < D; ++k)
       if (k < d) add_pair<S>(sum0, sum1, g[j][k]);
+    if (h0) {
+      if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
+      const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);
+      if (lane == 0) {
+        uint32_t* px = xh + n0 + v;
+        *px = t.a0 == kFull ? hard : (__ldg(px) & ~t.a0) | (hard & t.a0);
+      }
+    }
+    if (h1) {
+      if (t.s1) lv[(n1 + v) * kLanes + lane] = sum1;
+      const uint32_t hard = __ballot_sync(kFull, sum1 < 0.f);
+      if (lane == 1) {
+        uint32_t* px = xh + n1 + v;
+        *px = t.a1 == kFull ? hard : (__ldg(px) & ~t.a1) | (hard & t.a1);
+      }
+    }
+  }
+}
+
+// vn_rows_kernel for a tile pair (FP16 / BF16 messages, whose row-form magnitudes
+// are stored rounded to the message type): each lane sums its frame in both
+// tiles.
+template <int D>
+__global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int cls, float* __restrict__ lv,
+                                                           const uint32_t* __restrict__ yt,
+                                                           const float* __restrict__ ymag, uint32_t* __restrict__ xh,
+                                                           const uint32_t* __restrict__ active, int n_tiles,
+                                                           const float* __restrict__ fmag,
+                                                           const uint32_t* __restrict__ rsgn) {
+  __shared__ float fm[2][kMaxRowDeg * kLanes];
+  const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
+  if ((t.a0 | t.a1) == 0) return;
+  const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
+  for (int i = threadIdx.x; i < c.max_row_deg * kLanes; i += blockDim.x) {
+    fm[0][i] = h0 ? fmag[int64_t(t.t0) * kMaxRowDeg * kLanes + i] : 0.f;
+    fm[1][i] = h1 ? fmag[int64_t(t.t1) * kMaxRowDeg * kLanes + i] : 0.f;
+  }
+  __syncthreads();
+  const int d = c.vclass_deg[cls], N = kLanes / d;
+  const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
+  const int q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
+  if (q0 >= count) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = min(N, count - q0);
+  const bool on = lane < cnt * d;
+  const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
+  const uint32_t rs0 = on && h0 ? __ldg(rsgn + int64_t(t.t0) * c.m_tot + (e >> 6)) : 0u;
+  const uint32_t rs1 = on && h1 ? __ldg(rsgn + int64_t(t.t1) * c.m_tot + (e >> 6)) : 0u;
+  const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
+  const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
+  const uint32_t my0 = lane < cnt && h0 ? __ldg(yt + n0 + mycol) : 0u;
+  const uint32_t my1 = lane < cnt && h1 ? __ldg(yt + n1 + mycol) : 0u;
+  const float ym0 = h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
+  const float ym1 = h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
+  for (int j = 0; j < cnt; ++j) {
+    const int v = __shfl_sync(kFull, mycol, j);
+    const uint32_t y0 = __shfl_sync(kFull, my0, j), y1 = __shfl_sync(kFull, my1, j);
+    float sum0 = ((y0 >> lane) & 1u) ? -ym0 : ym0;
+    float sum1 = ((y1 >> lane) & 1u) ? -ym1 : ym1;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) {
+        const int src = j * d + k;
+        const uint32_t r0 = __shfl_sync(kFull, rs0, src), r1 = __shfl_sync(kFull, rs1, src);
+        const int dg = __shfl_sync(kFull, e, src) & 63;
+        sum0 += row_msg(fm[0][dg * kLanes + lane], r0, y0, lane);
+        sum1 += row_msg(fm[1][dg * kLanes + lane], r1, y1, lane);
+      }
     if (h0) {
       if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
       const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);

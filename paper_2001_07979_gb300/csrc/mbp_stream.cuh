@@ -39,20 +39,32 @@ constexpr int cn_min_blocks(int dmax) {
 
 // One warp per (tile, check row): 8 rows per block, tile = blockIdx.y, rows
 // p0 .. p1 - 1 (every row for flooding, one matrix's rows for the serial order).
-template <typename M, typename S, int DMAX, bool FIXED>
+// RIN: iteration 2 after a row-form iteration 1 (the old messages are rebuilt
+// from fmag / rsgn and Bob's sign words yt); the kernel then clears the row-form
+// flag counters[2], as the messages are per edge again.
+template <typename M, typename S, int DMAX, bool FIXED, bool RIN = false>
 __global__ void __launch_bounds__(256, cn_min_blocks<M>(DMAX)) cn_kernel(const DevCode c, int p0, int p1, int first_iter,
                                                  S* __restrict__ c2v, const M* __restrict__ lsrc,
                                                  const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                                  const uint32_t* __restrict__ zt,
                                                  const uint32_t* __restrict__ active, M l_max,
-                                                 int32_t* __restrict__ lacc, float qscale) {
+                                                 int32_t* __restrict__ lacc, float qscale,
+                                                 const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn,
+                                                 int32_t* __restrict__ counters) {
+  if (RIN && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[2] = 0;
   const int tile = blockIdx.y;
   const uint32_t act = active[tile];
   if (act == 0) return;
   const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
   if (p >= p1) return;
-  cn_tile_row<M, S, DMAX, FIXED, kPolStream>(c, tile, p, act, first_iter, c2v, lsrc, yt, ymag, zt, l_max,
-                                          Arith<M>::delta(l_max), lacc, qscale);
+  CnView<M, S> v = cn_view<M, S, kPolStream>(c, tile, act, first_iter, c2v, lsrc, yt, ymag, zt,
+                                             FIXED ? lacc : nullptr);
+  if constexpr (RIN) {
+    v.rm = fmag + int64_t(tile) * kMaxRowDeg * kLanes + (threadIdx.x & 31);
+    v.rs = rsgn + int64_t(tile) * c.m_tot;
+    v.yprev = yt + int64_t(tile) * c.n;
+  }
+  cn_view_row<M, S, DMAX, FIXED, kPolStream, RIN>(v, p, first_iter, l_max, Arith<M>::delta(l_max), qscale);
 }
 
 // Iteration 1 of BSC inputs in a kernel of its own (sign words in, messages
@@ -79,6 +91,45 @@ __global__ void __launch_bounds__(256) cn_first_kernel(const DevCode c, int p0, 
   const M inv = Arith<M>::delta(l_max);  // d_lmax
   if (deg == DMAX) cn_row_signs<M, S, DMAX, false, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
   else cn_row_signs<M, S, DMAX, true, kPolStream>(deg, cols, ysrc, ym, msg, par, store, l_max, inv);
+}
+
+// Iteration 1 of BSC inputs in row form (DevState::fmag), part 1: the sign word of
+// each row, z_j xor the row's parity of Bob's bits, for the 32 frames of a tile at
+// once (one thread per (tile, row)); the kernel sets the row-form flag counters[2].
+template <int DMAX>
+__global__ void __launch_bounds__(256) first_rows_kernel(const DevCode c, const uint32_t* __restrict__ yt,
+                                                         const uint32_t* __restrict__ zt,
+                                                         const uint32_t* __restrict__ active,
+                                                         uint32_t* __restrict__ rsgn, int32_t* __restrict__ counters) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[2] = 1;
+  const int tile = blockIdx.y;
+  if (active[tile] == 0) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.m_tot) return;
+  const int base = c.slice_base[p];
+  const int deg = c.slice_base[p + 1] - base;
+  int col[DMAX];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(c.slot_col + base + k) : -1;
+  const uint32_t* y = yt + int64_t(tile) * c.n;
+  uint32_t w = zt[int64_t(tile) * c.m_tot + p];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k)
+    if (col[k] >= 0) w ^= __ldg(y + col[k]);
+  rsgn[int64_t(tile) * c.m_tot + p] = w;
+}
+
+// Part 2: the output magnitude of a row of degree d (the same for every row of
+// that degree: all of a frame's inputs have the magnitude ln((1 - e)/e)), per
+// frame, rounded to the message type: fmag[tile][d - 1][lane].
+template <typename M, typename S>
+__global__ void first_mag_kernel(int n_tiles, int max_deg, const M* __restrict__ ymag, M l_max,
+                                 M* __restrict__ fmag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (tile, degree - 1, lane)
+  if (i >= n_tiles * max_deg * kLanes) return;
+  const int lane = i % kLanes, d = (i / kLanes) % max_deg, tile = i / (kLanes * max_deg);
+  fmag[(int64_t(tile) * kMaxRowDeg + d) * kLanes + lane] =
+      row_mag<M, S>(cn_first_mag_any<M>(d + 1, ymag[tile * kLanes + lane], l_max, Arith<M>::delta(l_max)));
 }
 
 // The min-sum check rule (variant), FP32 arithmetic; same layout as cn_kernel.
@@ -115,6 +166,9 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __res
 // The same update for the nodes of one degree class (DevCode::vclass_*): a
 // node and its slots are loaded together (one dependent round trip fewer), and
 // a warp takes N nodes of degree <= D so that about 16 gathers are in flight.
+// The same update for the nodes of one degree class (DevCode::vclass_*): a
+// node and its slots are loaded together (one dependent round trip fewer), and
+// a warp takes N nodes of degree <= D so that about 16 gathers are in flight.
 template <typename M, typename S, int D, int N>
 __global__ void __launch_bounds__(256) vn_class_kernel(const DevCode c, int cls, const S* __restrict__ c2v,
                                                        M* __restrict__ lv, const M* __restrict__ lp,
@@ -137,12 +191,99 @@ __global__ void __launch_bounds__(256) vn_class_kernel(const DevCode c, int cls,
   }
 }
 
+// Eq. (2) in iteration 1 when its messages are in row form (fmag / rsgn, BSC
+// inputs): a warp takes the N = 32 / d nodes of one class (degree d <= D <= 16)
+// whose N d edges fit its lanes. Lane l fetches edge l % d of node l / d -- its
+// row entry (DevCode::vrow, one coalesced load) and that row's sign word (one
+// gather) -- and each node then sums its edges in stacked-row order, taking every
+// edge's word from its lane (shuffles) and the magnitude of the row's degree from
+// the tile's table in shared memory.
+template <typename M, int D>
+__global__ void __launch_bounds__(256) vn_rows_kernel(const DevCode c, int cls, M* __restrict__ lv,
+                                                      const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
+                                                      uint32_t* __restrict__ xh, const uint32_t* __restrict__ active,
+                                                      const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn) {
+  __shared__ M fm[kMaxRowDeg * kLanes];
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  for (int i = threadIdx.x; i < c.max_row_deg * kLanes; i += blockDim.x)
+    fm[i] = fmag[int64_t(tile) * kMaxRowDeg * kLanes + i];
+  __syncthreads();
+  const int d = c.vclass_deg[cls], N = kLanes / d;
+  const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
+  const int q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
+  if (q0 >= count) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = min(N, count - q0);
+  const bool on = lane < cnt * d;
+  const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
+  const uint32_t rs = on ? __ldg(rsgn + int64_t(tile) * c.m_tot + (e >> 6)) : 0u;
+  const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
+  const uint32_t myy = lane < cnt ? __ldg(yt + int64_t(tile) * c.n + mycol) : 0u;
+  const M ym = __ldg(ymag + tile * kLanes + lane);
+  const int64_t node0 = int64_t(tile) * c.n;
+  for (int j = 0; j < cnt; ++j) {
+    const int col = __shfl_sync(kFull, mycol, j);
+    const uint32_t yv = __shfl_sync(kFull, myy, j);
+    M sum = ((yv >> lane) & 1u) ? -ym : ym;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) {
+        const uint32_t r = __shfl_sync(kFull, rs, j * d + k);
+        const int dg = __shfl_sync(kFull, e, j * d + k) & 63;
+        sum += row_msg(fm[dg * kLanes + lane], r, yv, lane);
+      }
+    if ((act >> lane) & 1u) lv[(node0 + col) * kLanes + lane] = sum;
+    const uint32_t hard = __ballot_sync(kFull, sum < M(0));
+    if (lane == 0) {
+      uint32_t* px = xh + node0 + col;
+      *px = act == kFull ? hard : (__ldg(px) & ~act) | (hard & act);
+    }
+  }
+}
+
+// Whether iteration 1 of a flooding sum-product decode keeps its messages in row
+// form (DevState::fmag): BSC inputs (one channel magnitude per frame) and every
+// variable-node class of at most 16 edges.
+inline bool rows_ok(const DevCode& c, const DevState& st) {
+  return st.yt && st.fmag && c.vrow && c.n_vclass > 0 && c.vclass_deg[c.n_vclass - 1] <= 16 &&
+         c.max_row_deg <= 32;
+}
+
 // Eq. (2) for every node of every unfinished tile: one launch per degree class, or one over all nodes.
+// rows: iteration 1 in row form (rows_ok).
 template <typename M, typename S>
-void launch_vn(const DevCode& c, const DevState& st, cudaStream_t s) {
+void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) {
   if (c.n_vclass > 0) {
     for (int k = 0; k < c.n_vclass; ++k) {
       const int count = c.vclass_first[k + 1] - c.vclass_first[k], d = c.vclass_deg[k];
+      if (rows) {  // classes of up to 16 edges (rows_ok), 32 / d nodes per warp
+        const int per_warp = kLanes / d;
+        const unsigned blocks = blocks_for(count, 8 * per_warp);
+        if constexpr (sizeof(S) == 2) {
+          const unsigned pairs = unsigned((st.n_tiles + 1) / 2);
+#define MBP_VR2(D)                                                                                             \
+  vn_rows_pair_kernel<D><<<dim3(blocks, pairs), 256, 0, s>>>(c, k, static_cast<float*>(st.lv), st.yt,             \
+                                                             static_cast<const float*>(st.chan_mag), st.xh,       \
+                                                             st.active, st.n_tiles,                               \
+                                                             static_cast<const float*>(st.fmag), st.rsgn)
+          if (d <= 4) MBP_VR2(4);
+          else if (d <= 8) MBP_VR2(8);
+          else MBP_VR2(16);
+#undef MBP_VR2
+        } else {
+#define MBP_VR(D)                                                                                              \
+  vn_rows_kernel<M, D><<<dim3(blocks, st.n_tiles), 256, 0, s>>>(c, k, static_cast<M*>(st.lv), st.yt,             \
+                                                                static_cast<const M*>(st.chan_mag), st.xh,        \
+                                                                st.active, static_cast<const M*>(st.fmag), st.rsgn)
+          if (d <= 4) MBP_VR(4);
+          else if (d <= 8) MBP_VR(8);
+          else MBP_VR(16);
+#undef MBP_VR
+        }
+        continue;
+      }
       if constexpr (sizeof(S) == 2) {  // tile pairs for classes of up to 16 edges
         const unsigned pairs = unsigned((st.n_tiles + 1) / 2);
 #define MBP_VN2(D, N)                                                                                         \
@@ -220,16 +361,31 @@ __global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, in
 
 // Rows p0 .. p1 - 1 of every tile that is still decoding, from the posterior (or L_P) lsrc, or from the sign
 // words yt in the first iteration of BSC inputs.
+// rows: 1 = iteration 1 writes its messages in row form, 2 = iteration 2 reads
+// the previous messages in row form, 0 = per edge.
 struct CnLaunch {
   int p0, p1, first_iter;
   const void* lsrc;
   const uint32_t* yt;
+  int rows;
 };
 
 template <typename M, typename S, int DMAX, bool FIXED>
 void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l_max, float qscale, int rule,
                cudaStream_t s) {
   const dim3 grid(blocks_for(q.p1 - q.p0, 8), st.n_tiles);
+  if constexpr (!FIXED && DMAX <= 32) {
+    if (q.rows == 1) {  // iteration 1 in row form: the rows' sign words and the magnitude table
+      first_rows_kernel<DMAX><<<dim3(blocks_for(c.m_tot, 256), st.n_tiles), 256, 0, s>>>(c, q.yt, st.zt, st.active,
+                                                                                        st.rsgn, st.counters);
+      const int cells = st.n_tiles * c.max_row_deg * kLanes;
+      first_mag_kernel<M, S><<<blocks_for(cells, 256), 256, 0, s>>>(st.n_tiles, c.max_row_deg,
+                                                                   static_cast<const M*>(st.chan_mag), M(l_max),
+                                                                   static_cast<M*>(st.fmag));
+      return;
+    }
+  }
+  const M* rm_in = q.rows == 2 ? static_cast<const M*>(st.fmag) : nullptr;
   if constexpr (sizeof(S) == 2 && !FIXED && DMAX <= 24) {  // tile pairs (mbp_pair.cuh)
     if (rule == MBP_RULE_SUM_PRODUCT) {
       const dim3 pgrid(grid.x, unsigned((st.n_tiles + 1) / 2));
@@ -237,10 +393,16 @@ void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l
         cn_first_pair_kernel<S, DMAX><<<pgrid, 256, 0, s>>>(c, q.p0, q.p1, static_cast<S*>(st.c2v), q.yt,
                                                             static_cast<const float*>(st.chan_mag), st.zt, st.active,
                                                             st.n_tiles, float(l_max));
+      else if (rm_in)
+        cn_pair_kernel<S, DMAX, true><<<pgrid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
+                                                            static_cast<const float*>(q.lsrc), st.zt, st.active,
+                                                            st.n_tiles, float(l_max), rm_in, st.rsgn, st.yt,
+                                                            st.counters);
       else
-        cn_pair_kernel<S, DMAX><<<pgrid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
-                                                      static_cast<const float*>(q.lsrc), st.zt, st.active,
-                                                      st.n_tiles, float(l_max));
+        cn_pair_kernel<S, DMAX, false><<<pgrid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
+                                                             static_cast<const float*>(q.lsrc), st.zt, st.active,
+                                                             st.n_tiles, float(l_max), nullptr, nullptr, nullptr,
+                                                             st.counters);
       return;
     }
   }
@@ -261,10 +423,19 @@ void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l
       return;
     }
   }
+  if constexpr (!FIXED && DMAX <= 32) {
+    if (rm_in) {
+      cn_kernel<M, S, DMAX, false, true><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
+                                                              static_cast<const M*>(q.lsrc), st.yt,
+                                                              static_cast<const M*>(st.chan_mag), st.zt, st.active,
+                                                              M(l_max), st.lacc, qscale, rm_in, st.rsgn, st.counters);
+      return;
+    }
+  }
   cn_kernel<M, S, DMAX, FIXED><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
                                                  static_cast<const M*>(q.lsrc), q.yt,
                                                  static_cast<const M*>(st.chan_mag), st.zt, st.active, M(l_max),
-                                                 st.lacc, qscale);
+                                                 st.lacc, qscale, nullptr, nullptr, st.counters);
 }
 
 // Unroll bound at or one above the largest check degree (the last two degrees run without per-edge tests).
@@ -300,16 +471,18 @@ void launch_cn_any(const DevCode& c, const DevState& st, const CnLaunch& q, doub
 // grouped decode): eq. (6) over every row, eq. (2) and the hard decision, and the stopping test; the caller
 // retires the finished frames.
 template <typename M, typename S>
-cudaError_t group_step(const DevCode& c, const DevState& st, int first_iter, double l_max, cudaStream_t s) {
+// iter: 1, 2, or 0 for any later iteration (iterations 1 and 2 differ in where their messages come from).
+cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s) {
   const int NT = st.n_tiles;
-  const CnLaunch q{0, c.m_tot, first_iter, first_iter ? st.lp : st.lv, st.yt};
+  const bool rows = rows_ok(c, st);
+  const CnLaunch q{0, c.m_tot, iter == 1, iter == 1 ? st.lp : st.lv, st.yt, rows ? (iter == 1 || iter == 2 ? iter : 0) : 0};
   prof_begin(MBP_KERNEL_CHECK, s);
   launch_cn_any<M, S, false>(c, st, q, l_max, 0.f, MBP_RULE_SUM_PRODUCT, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   prof_end(MBP_KERNEL_CHECK, s, 1);
   prof_begin(MBP_KERNEL_VARIABLE, s);
-  launch_vn<M, S>(c, st, s);
+  launch_vn<M, S>(c, st, rows && iter == 1, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_end(MBP_KERNEL_VARIABLE, s, c.n_vclass > 0 ? c.n_vclass : 1);
   prof_begin(MBP_KERNEL_SYNDROME, s);
@@ -358,14 +531,14 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
   if (a.early_exit || a.max_iter == 0) {
     if ((rc = stop_check(0, &left))) return rc;
   }
-  auto variable = [&]() -> int {
+  auto variable = [&](bool rows) -> int {
     prof_begin(MBP_KERNEL_VARIABLE, s);
     if (fixed)
       finalize_kernel<M><<<node_grid, 256, 0, s>>>(c, st.lacc, static_cast<M*>(st.lv), static_cast<const M*>(st.lp),
                                                    st.yt, static_cast<const M*>(st.chan_mag), st.xh, st.active,
                                                    inv_qscale);
     else
-      launch_vn<M, S>(c, st, s);
+      launch_vn<M, S>(c, st, rows, s);
     CKL("vn_kernel");
     prof_end(MBP_KERNEL_VARIABLE, s, fixed || c.n_vclass == 0 ? 1 : c.n_vclass);
     return MBP_OK;
@@ -383,6 +556,7 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
     return MBP_OK;
   };
   const bool serial = a.update == MBP_UPDATE_MATRIX_SERIAL && c.u > 1;
+  const bool rows = !fixed && !serial && a.rule == MBP_RULE_SUM_PRODUCT && rows_ok(c, st);
   if (serial && a.max_iter > 0 && left > 0)  // matrices not yet visited in iteration 1 contribute 0 to eq. (2)
     CK(cudaMemsetAsync(st.c2v, 0, msg_tiles(NT, sizeof(S)) * c.s_tot * kLanes * sizeof(S), s), "clear messages");
   for (int t = 1; t <= a.max_iter && left > 0; ++t) {
@@ -390,14 +564,15 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
       // Algorithm 1's nesting: each matrix's checks, then eq. (2) with its new messages, before the next matrix
       for (int l = 0; l < c.u; ++l) {
         const bool from_lp = t == 1 && l == 0;
-        const CnLaunch q{c.row_pos[l], c.row_pos[l + 1], t == 1, from_lp ? st.lp : st.lv, from_lp ? st.yt : nullptr};
+        const CnLaunch q{c.row_pos[l], c.row_pos[l + 1], t == 1, from_lp ? st.lp : st.lv, from_lp ? st.yt : nullptr,
+                         0};
         if ((rc = check(q))) return rc;
-        if ((rc = variable())) return rc;
+        if ((rc = variable(false))) return rc;
       }
     } else {
-      const CnLaunch q{0, c.m_tot, t == 1, t == 1 ? st.lp : st.lv, st.yt};
+      const CnLaunch q{0, c.m_tot, t == 1, t == 1 ? st.lp : st.lv, st.yt, rows ? (t <= 2 ? t : 0) : 0};
       if ((rc = check(q))) return rc;
-      if ((rc = variable())) return rc;
+      if ((rc = variable(rows && t == 1))) return rc;
     }
     if (a.early_exit || t == a.max_iter) {
       if ((rc = stop_check(t, &left))) return rc;
