@@ -82,19 +82,27 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(iters, n, e_tot, msg_bytes=4):
-    """Floor bytes of the frame-iterations run, for the check kernel and for the whole path.
+def algorithmic_bytes(iters, n, e_tot, msg_bytes=4, rows=False):
+    """Floor bytes of the frame-iterations run, for the per-edge check kernel and for the whole path.
 
-    Every iteration writes each message once and reads the posterior once (check
-    kernel: s E + 4 n); every iteration after a frame's first also reads the
-    previous messages (s E). The whole path adds writing and re-reading the
-    posterior (8 n): 2 s E + 12 n per iteration after the first.
+    A per-edge check iteration writes each message once and reads the posterior
+    once (s E + 4 n), and after a frame's first iteration also reads the previous
+    messages (s E). With the row form (BSC inputs) iterations 1 and 2 run as
+    row-form check work of their own (their bytes are not the per-edge kernel's),
+    and the per-edge kernel runs from iteration 3 on: 2 s E + 4 n each. The
+    whole path adds the variable-node pass, which reads the messages and writes
+    the posterior: per frame, 4 n in iteration 1 (row form) or 2 s E + 8 n
+    (per edge), 2 s E + 8 n in iteration 2 (row form) and 3 s E + 8 n later.
     """
     it = np.asarray(iters, dtype=np.int64)
-    later = np.maximum(it - 1, 0)
     sE = msg_bytes * e_tot
-    check = int(np.sum(it * (sE + 4 * n) + later * sE))
-    path = int(np.sum(it * (sE + 12 * n) + later * sE))
+    if rows:
+        check = int(np.sum(np.maximum(it - 2, 0) * (2 * sE + 4 * n)))
+        path = int(np.sum((it >= 1) * 4 * n + (it >= 2) * (2 * sE + 8 * n) + np.maximum(it - 2, 0) * (3 * sE + 8 * n)))
+    else:
+        later = np.maximum(it - 1, 0)
+        check = int(np.sum(it * (sE + 4 * n) + later * sE))
+        path = int(np.sum((it >= 1) * (2 * sE + 8 * n) + later * (3 * sE + 8 * n)))
     return check, path
 
 
@@ -183,7 +191,8 @@ def oracle_time(H, x, y, e, frames, threads):
     return dt, out
 
 
-KERNEL_SOURCES = ("mbp_internal.h", "mbp_device.cuh", "mbp_stream.cuh", "mbp_stream_f32.cu", "mbp_resident.cuh")
+KERNEL_SOURCES = ("mbp_internal.h", "mbp_device.cuh", "mbp_stream.cuh", "mbp_pair.cuh", "mbp_stream_f32.cu",
+                  "mbp_resident.cuh")
 
 
 def kernel_source_digest():
@@ -195,7 +204,7 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def kernel_traffic(iters, launches, summary, msg_dtype):
+def kernel_traffic(iters, launches, summary, msg_dtype, rows=False):
     """Mean DRAM bytes per launch of the dominant kernel, from the committed full-size ncu capture (bytes per
     frame in a frame's first iteration and in a later one), if that capture was taken on the current source
     with the same message type."""
@@ -209,9 +218,12 @@ def kernel_traffic(iters, launches, summary, msg_dtype):
         if kv.get("msg_dtype", "f32") != msg_dtype:
             return None
         it = np.asarray(iters, dtype=np.int64)
-        first, later = int(np.sum(it >= 1)), int(np.sum(np.maximum(it - 1, 0)))
-        total = first * float(kv["dram_bytes_per_frame_first_iteration"]) + \
-            later * float(kv["dram_bytes_per_frame_later_iteration"])
+        if rows:  # the per-edge kernel runs the iterations after the second
+            total = int(np.sum(np.maximum(it - 2, 0))) * float(kv["dram_bytes_per_frame_later_iteration"])
+        else:
+            first, later = int(np.sum(it >= 1)), int(np.sum(np.maximum(it - 1, 0)))
+            total = first * float(kv["dram_bytes_per_frame_first_iteration"]) + \
+                later * float(kv["dram_bytes_per_frame_later_iteration"])
         return total / launches
     except Exception:
         return None
@@ -362,9 +374,10 @@ def run_gb300(args):
 
     # roofline of the dominant kernel: algorithmic bytes of the frame-iterations it ran / its event time
     e_tot = codes.edges
-    b_check, b_path = algorithmic_bytes(iters, N, e_tot, msg_bytes)  # one step
+    rows = prof.get("check_rows", (0, 0.0))[0] > 0  # iterations 1 and 2 ran in row form
+    b_check, b_path = algorithmic_bytes(iters, N, e_tot, msg_bytes, rows)  # one step
     peak, peak_src = load_peaks()
-    dominant = max(prof, key=lambda k: prof[k][1])
+    dominant = "persistent" if prof.get("persistent", (0, 0.0))[0] > 0 else "check"
     launches = int(sum(v[0] for v in prof.values()))
     path_gbs = b_path / (ms / 1e3) / 1e9
     if dominant == "persistent":
@@ -375,9 +388,12 @@ def run_gb300(args):
         traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "resident_kernel_n65536.txt", args.msg_dtype)
     else:
         n_dom, ms_dom = prof["check"]
-        kernel_name = "cn_kernel (check-node update, eq. 6)"
-        b_dom, rule = b_check, "per frame: s*E+4n per iteration, plus s*E per iteration after the first"
-        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "check_node_kernel_n65536.txt", args.msg_dtype)
+        kernel_name = "cn_kernel (check-node update, eq. 6, per-edge messages)"
+        rule = ("per frame: 2*s*E+4n per iteration after the second (iterations 1 and 2 run in row form)" if rows
+                else "per frame: s*E+4n per iteration, plus s*E per iteration after the first")
+        b_dom = b_check
+        traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "check_node_kernel_n65536.txt",
+                                 args.msg_dtype, rows)
     achieved = b_dom * args.steps / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else None
 
     result = None
@@ -404,7 +420,10 @@ def run_gb300(args):
                          "mean_launch_ms": ms_dom / n_dom if n_dom else None,
                          "dominant_family": dominant,
                          "path_gbs": path_gbs, "path_frac": path_gbs / peak,
-                         "path_bytes_rule": "2*s*E+12n per frame-iteration (s*E less in a frame's first)"},
+                         "path_bytes_rule": ("per frame: 4n (iteration 1, row form), 2*s*E+8n (iteration 2), "
+                                             "3*s*E+8n later" if rows else
+                                             "per frame: 2*s*E+8n (iteration 1), 3*s*E+8n later"),
+                         "row_form": rows},
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()},
             "kernel_ms_source": "a second pass of the same steps with a CUDA event pair around every kernel launch",
             "gpu_launches": launches,

@@ -412,7 +412,10 @@ enum {
   MBP_KERNEL_SETUP = 4,     /* channel LLRs, syndrome bits and tile state into the workspace */
   MBP_KERNEL_OUTPUT = 5,    /* output bits and soft values */
   MBP_KERNEL_PERSISTENT = 6,/* the resident schedule's single kernel (all steps of every iteration) */
-  MBP_KERNEL_FAMILIES = 7
+  MBP_KERNEL_CHECK_ROWS = 7,/* eq. (6) in iteration 1 of BSC inputs, kept in row form (one sign word per
+                               check and one magnitude per check degree and frame), and in iteration 2,
+                               which reads the previous messages from that form */
+  MBP_KERNEL_FAMILIES = 8
 };
 int mbp_profile_enable(int on);
 int mbp_profile_get(int family, int64_t* launches, double* milliseconds);

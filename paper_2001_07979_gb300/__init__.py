@@ -539,7 +539,7 @@ class NBPDecoder(torch.nn.Module):
         return NormalizedBP.apply(llr, self.alpha, self.beta, self.codes, z_bits, self.l_max)
 
 
-KERNEL_FAMILIES = ("check", "variable", "syndrome", "retire", "setup", "output", "persistent")
+KERNEL_FAMILIES = ("check", "variable", "syndrome", "retire", "setup", "output", "persistent", "check_rows")
 
 
 def mbp_profile_enable(on: bool = True):

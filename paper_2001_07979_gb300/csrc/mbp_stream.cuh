@@ -476,11 +476,12 @@ cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_
   const int NT = st.n_tiles;
   const bool rows = rows_ok(c, st);
   const CnLaunch q{0, c.m_tot, iter == 1, iter == 1 ? st.lp : st.lv, st.yt, rows ? (iter == 1 || iter == 2 ? iter : 0) : 0};
-  prof_begin(MBP_KERNEL_CHECK, s);
+  const int fam = q.rows ? MBP_KERNEL_CHECK_ROWS : MBP_KERNEL_CHECK;
+  prof_begin(fam, s);
   launch_cn_any<M, S, false>(c, st, q, l_max, 0.f, MBP_RULE_SUM_PRODUCT, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  prof_end(MBP_KERNEL_CHECK, s, 1);
+  prof_end(fam, s, q.rows == 1 ? 2 : 1);
   prof_begin(MBP_KERNEL_VARIABLE, s);
   launch_vn<M, S>(c, st, rows && iter == 1, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -544,7 +545,8 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
     return MBP_OK;
   };
   auto check = [&](const CnLaunch& q) -> int {
-    prof_begin(MBP_KERNEL_CHECK, s);
+    const int fam = q.rows ? MBP_KERNEL_CHECK_ROWS : MBP_KERNEL_CHECK;
+    prof_begin(fam, s);
     if constexpr (sizeof(M) == 4 && sizeof(S) == 4) {
       if (fixed) launch_cn_any<M, S, true>(c, st, q, l_max, qscale, a.rule, s);
       else launch_cn_any<M, S, false>(c, st, q, l_max, qscale, a.rule, s);
@@ -552,7 +554,7 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
       launch_cn_any<M, S, false>(c, st, q, l_max, qscale, a.rule, s);
     }
     CKL("cn_kernel");
-    prof_end(MBP_KERNEL_CHECK, s, 1);
+    prof_end(fam, s, q.rows == 1 ? 2 : 1);
     return MBP_OK;
   };
   const bool serial = a.update == MBP_UPDATE_MATRIX_SERIAL && c.u > 1;
