@@ -281,9 +281,13 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
         row_mat[r] = static_cast<uint8_t>(l);
       }
   }
-  int32_t max_deg = 0;
-  for (int64_t r = 0; r < m_tot; ++r) max_deg = std::max(max_deg, row_deg[r]);
+  int32_t max_deg = 0, min_deg = 0;
+  for (int64_t r = 0; r < m_tot; ++r) {
+    max_deg = std::max(max_deg, row_deg[r]);
+    if (row_deg[r] > 0) min_deg = min_deg == 0 ? row_deg[r] : std::min(min_deg, row_deg[r]);
+  }
   d.max_row_deg = max_deg;
+  d.min_row_deg = min_deg > 0 ? min_deg : 1;
   // The decoder visits the stacked rows matrix by matrix, each matrix's rows in
   // degree order (ties keep the stacked order): row position p owns the slots
   // slice_base[p] .. slice_base[p+1] - 1, and matrix l's rows are the positions

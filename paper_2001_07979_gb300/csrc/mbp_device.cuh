@@ -261,6 +261,22 @@ __device__ __forceinline__ M row_msg(M rm, uint32_t rs, uint32_t y, int lane) {
   return Bits<M>::copy_sign(rm, (rs ^ y) << (31 - lane));
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane i holds row i (bit j =
+// A[i][j]); afterwards lane j holds column j (bit i = A[i][j]). Five exchange
+// rounds of block sizes 16, 8, 4, 2, 1, each swapping the off-diagonal blocks.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t a) {
+  const int lane = threadIdx.x & 31;
+  constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int s = 16 >> r;
+    const uint32_t m = kMask[r];
+    const uint32_t o = __shfl_xor_sync(kFull, a, s);
+    a = (lane & s) ? ((a & ~m) | ((o & ~m) >> s)) : ((a & m) | ((o & m) << s));
+  }
+  return a;
+}
+
 // The first-iteration row of BSC inputs (see cn_first_mag): each edge takes the
 // shared magnitude with the sign of the other edges' bits and z_j. The row's
 // bits are kept as one mask (D <= 32), edges k >= deg are padding.

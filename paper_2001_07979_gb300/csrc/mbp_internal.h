@@ -48,6 +48,7 @@ constexpr size_t msg_tiles(size_t n_tiles, size_t msg_bytes) {
 struct DevCode {
   int32_t n, u, m_tot;
   int32_t max_row_deg;
+  int32_t min_row_deg;  // smallest degree of a check with edges (1 when there are none)
   int32_t max_col_deg;
   int64_t e_tot, s_tot;
   int32_t m[kMaxU];

@@ -445,5 +445,87 @@ __global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int 
   }
 }
 
+// vn_rows4_kernel (check degrees within 4 values) for a tile pair: one bit
+// transpose per tile, the degree offsets from two ballots, each tile's four
+// magnitudes in registers.
+template <int D, int NB>
+__global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int cls, float* __restrict__ lv,
+                                                            const uint32_t* __restrict__ yt,
+                                                            const float* __restrict__ ymag, uint32_t* __restrict__ xh,
+                                                            const uint32_t* __restrict__ active, int n_tiles,
+                                                            const float* __restrict__ fmag,
+                                                            const uint32_t* __restrict__ rsgn) {
+  static_assert(NB == 1 || NB == 2, "check degrees within 2 or 4 values");
+  const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
+  if ((t.a0 | t.a1) == 0) return;
+  const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
+  const int d = c.vclass_deg[cls], N = kLanes / d;
+  const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
+  const int q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
+  if (q0 >= count) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = min(N, count - q0);
+  const bool on = lane < cnt * d;
+  const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
+  const uint32_t T0 = warp_transpose32(on && h0 ? __ldg(rsgn + int64_t(t.t0) * c.m_tot + (e >> 6)) : 0u);
+  const uint32_t T1 = warp_transpose32(on && h1 ? __ldg(rsgn + int64_t(t.t1) * c.m_tot + (e >> 6)) : 0u);
+  const int rel = on ? (e & 63) + 1 - c.min_row_deg : 0;  // 0 .. 2^NB - 1
+  const uint32_t b0 = __ballot_sync(kFull, rel & 1), b1 = NB > 1 ? __ballot_sync(kFull, (rel >> 1) & 1) : 0u;
+  const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
+  const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
+  const uint32_t my0 = lane < cnt && h0 ? __ldg(yt + n0 + mycol) : 0u;
+  const uint32_t my1 = lane < cnt && h1 ? __ldg(yt + n1 + mycol) : 0u;
+  const int g0 = c.min_row_deg - 1;
+  float ma[1 << NB], mb[1 << NB];
+#pragma unroll
+  for (int i = 0; i < (1 << NB); ++i) {
+    const int g = min(g0 + i, kMaxRowDeg - 1);
+    ma[i] = h0 ? __ldg(fmag + (int64_t(t.t0) * kMaxRowDeg + g) * kLanes + lane) : 0.f;
+    mb[i] = h1 ? __ldg(fmag + (int64_t(t.t1) * kMaxRowDeg + g) * kLanes + lane) : 0.f;
+  }
+  const float ym0 = h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
+  const float ym1 = h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
+  for (int j = 0; j < cnt; ++j) {
+    const int v = __shfl_sync(kFull, mycol, j);
+    const uint32_t yl0 = (__shfl_sync(kFull, my0, j) >> lane) & 1u, yl1 = (__shfl_sync(kFull, my1, j) >> lane) & 1u;
+    float sum0 = yl0 ? -ym0 : ym0, sum1 = yl1 ? -ym1 : ym1;
+    const int base = j * d;
+    const uint32_t sg0 = (T0 ^ (0u - yl0)) >> base, sg1 = (T1 ^ (0u - yl1)) >> base;
+    const uint32_t r0 = b0 >> base, r1 = b1 >> base;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) {
+        const bool c0 = r0 & (1u << k);
+        float x0, x1;
+        if constexpr (NB == 1) {
+          x0 = c0 ? ma[1] : ma[0];
+          x1 = c0 ? mb[1] : mb[0];
+        } else {
+          const bool c1 = r1 & (1u << k);
+          x0 = c1 ? (c0 ? ma[3] : ma[2]) : (c0 ? ma[1] : ma[0]);
+          x1 = c1 ? (c0 ? mb[3] : mb[2]) : (c0 ? mb[1] : mb[0]);
+        }
+        sum0 += Bits<float>::copy_sign(x0, sg0 << (31 - k));
+        sum1 += Bits<float>::copy_sign(x1, sg1 << (31 - k));
+      }
+    if (h0) {
+      if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
+      const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);
+      if (lane == 0) {
+        uint32_t* px = xh + n0 + v;
+        *px = t.a0 == kFull ? hard : (__ldg(px) & ~t.a0) | (hard & t.a0);
+      }
+    }
+    if (h1) {
+      if (t.s1) lv[(n1 + v) * kLanes + lane] = sum1;
+      const uint32_t hard = __ballot_sync(kFull, sum1 < 0.f);
+      if (lane == 1) {
+        uint32_t* px = xh + n1 + v;
+        *px = t.a1 == kFull ? hard : (__ldg(px) & ~t.a1) | (hard & t.a1);
+      }
+    }
+  }
+}
+
 }  // namespace dev
 }  // namespace mbp

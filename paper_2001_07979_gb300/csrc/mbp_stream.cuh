@@ -243,6 +243,65 @@ __global__ void __launch_bounds__(256) vn_rows_kernel(const DevCode c, int cls, 
   }
 }
 
+// vn_rows_kernel for codes whose check degrees span at most 4 values (PEG codes:
+// a degree or two around the mean), without per-edge exchanges: one warp-wide
+// bit transpose of the edges' sign words gives each lane (frame) every edge's
+// sign bit, two ballots give every edge's degree offset from the smallest check
+// degree, and the four magnitudes of those degrees sit in registers; each edge
+// is then a few ALU instructions. Same values, same order as vn_rows_kernel.
+template <typename M, int D, int NB>
+__global__ void __launch_bounds__(256) vn_rows4_kernel(const DevCode c, int cls, M* __restrict__ lv,
+                                                       const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
+                                                       uint32_t* __restrict__ xh, const uint32_t* __restrict__ active,
+                                                       const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn) {
+  static_assert(NB == 1 || NB == 2, "check degrees within 2 or 4 values");
+  const int tile = blockIdx.y;
+  const uint32_t act = active[tile];
+  if (act == 0) return;
+  const int d = c.vclass_deg[cls], N = kLanes / d;
+  const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
+  const int q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
+  if (q0 >= count) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = min(N, count - q0);
+  const bool on = lane < cnt * d;
+  const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
+  const uint32_t T = warp_transpose32(on ? __ldg(rsgn + int64_t(tile) * c.m_tot + (e >> 6)) : 0u);
+  const int rel = on ? (e & 63) + 1 - c.min_row_deg : 0;  // 0 .. 2^NB - 1
+  const uint32_t b0 = __ballot_sync(kFull, rel & 1), b1 = NB > 1 ? __ballot_sync(kFull, (rel >> 1) & 1) : 0u;
+  const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
+  const int64_t node0 = int64_t(tile) * c.n;
+  const uint32_t myy = lane < cnt ? __ldg(yt + node0 + mycol) : 0u;
+  const M* fm = fmag + int64_t(tile) * kMaxRowDeg * kLanes + lane;
+  const int g0 = c.min_row_deg - 1;
+  M mg[1 << NB];
+#pragma unroll
+  for (int i = 0; i < (1 << NB); ++i) mg[i] = __ldg(fm + min(g0 + i, kMaxRowDeg - 1) * kLanes);
+  const M ym = __ldg(ymag + tile * kLanes + lane);
+  for (int j = 0; j < cnt; ++j) {
+    const int col = __shfl_sync(kFull, mycol, j);
+    const uint32_t yl = (__shfl_sync(kFull, myy, j) >> lane) & 1u;
+    M sum = yl ? -ym : ym;
+    // node j's edges at bits 0 .. d - 1: sign (Bob's bit folded in) and degree offset
+    const int base = j * d;
+    const uint32_t sg = (T ^ (0u - yl)) >> base, r0 = b0 >> base, r1 = b1 >> base;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < d) {
+        M m;
+        if constexpr (NB == 1) m = (r0 & (1u << k)) ? mg[1] : mg[0];
+        else m = (r1 & (1u << k)) ? ((r0 & (1u << k)) ? mg[3] : mg[2]) : ((r0 & (1u << k)) ? mg[1] : mg[0]);
+        sum += Bits<M>::copy_sign(m, sg << (31 - k));
+      }
+    if ((act >> lane) & 1u) lv[(node0 + col) * kLanes + lane] = sum;
+    const uint32_t hard = __ballot_sync(kFull, sum < M(0));
+    if (lane == 0) {
+      uint32_t* px = xh + node0 + col;
+      *px = act == kFull ? hard : (__ldg(px) & ~act) | (hard & act);
+    }
+  }
+}
+
 // Whether iteration 1 of a flooding sum-product decode keeps its messages in row
 // form (DevState::fmag): BSC inputs (one channel magnitude per frame) and every
 // variable-node class of at most 16 edges.
@@ -263,23 +322,42 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
         const unsigned blocks = blocks_for(count, 8 * per_warp);
         if constexpr (sizeof(S) == 2) {
           const unsigned pairs = unsigned((st.n_tiles + 1) / 2);
-#define MBP_VR2(D)                                                                                             \
-  vn_rows_pair_kernel<D><<<dim3(blocks, pairs), 256, 0, s>>>(c, k, static_cast<float*>(st.lv), st.yt,             \
-                                                             static_cast<const float*>(st.chan_mag), st.xh,       \
-                                                             st.active, st.n_tiles,                               \
-                                                             static_cast<const float*>(st.fmag), st.rsgn)
-          if (d <= 4) MBP_VR2(4);
-          else if (d <= 8) MBP_VR2(8);
-          else MBP_VR2(16);
+#define MBP_VR2(K, ...)                                                                                        \
+  K<__VA_ARGS__><<<dim3(blocks, pairs), 256, 0, s>>>(c, k, static_cast<float*>(st.lv), st.yt,                    \
+                                           static_cast<const float*>(st.chan_mag), st.xh, st.active, st.n_tiles, \
+                                           static_cast<const float*>(st.fmag), st.rsgn)
+          if (c.max_row_deg - c.min_row_deg <= 1) {
+            if (d <= 4) MBP_VR2(vn_rows4_pair_kernel, 4, 1);
+            else if (d <= 8) MBP_VR2(vn_rows4_pair_kernel, 8, 1);
+            else MBP_VR2(vn_rows4_pair_kernel, 16, 1);
+          } else if (c.max_row_deg - c.min_row_deg <= 3) {
+            if (d <= 4) MBP_VR2(vn_rows4_pair_kernel, 4, 2);
+            else if (d <= 8) MBP_VR2(vn_rows4_pair_kernel, 8, 2);
+            else MBP_VR2(vn_rows4_pair_kernel, 16, 2);
+          } else {
+            if (d <= 4) MBP_VR2(vn_rows_pair_kernel, 4);
+            else if (d <= 8) MBP_VR2(vn_rows_pair_kernel, 8);
+            else MBP_VR2(vn_rows_pair_kernel, 16);
+          }
 #undef MBP_VR2
         } else {
-#define MBP_VR(D)                                                                                              \
-  vn_rows_kernel<M, D><<<dim3(blocks, st.n_tiles), 256, 0, s>>>(c, k, static_cast<M*>(st.lv), st.yt,             \
-                                                                static_cast<const M*>(st.chan_mag), st.xh,        \
-                                                                st.active, static_cast<const M*>(st.fmag), st.rsgn)
-          if (d <= 4) MBP_VR(4);
-          else if (d <= 8) MBP_VR(8);
-          else MBP_VR(16);
+#define MBP_VR(K, ...)                                                                                         \
+  K<M, __VA_ARGS__><<<dim3(blocks, st.n_tiles), 256, 0, s>>>(c, k, static_cast<M*>(st.lv), st.yt,                \
+                                                   static_cast<const M*>(st.chan_mag), st.xh, st.active,           \
+                                                   static_cast<const M*>(st.fmag), st.rsgn)
+          if (c.max_row_deg - c.min_row_deg <= 1) {
+            if (d <= 4) MBP_VR(vn_rows4_kernel, 4, 1);
+            else if (d <= 8) MBP_VR(vn_rows4_kernel, 8, 1);
+            else MBP_VR(vn_rows4_kernel, 16, 1);
+          } else if (c.max_row_deg - c.min_row_deg <= 3) {
+            if (d <= 4) MBP_VR(vn_rows4_kernel, 4, 2);
+            else if (d <= 8) MBP_VR(vn_rows4_kernel, 8, 2);
+            else MBP_VR(vn_rows4_kernel, 16, 2);
+          } else {
+            if (d <= 4) MBP_VR(vn_rows_kernel, 4);
+            else if (d <= 8) MBP_VR(vn_rows_kernel, 8);
+            else MBP_VR(vn_rows_kernel, 16);
+          }
 #undef MBP_VR
         }
         continue;
