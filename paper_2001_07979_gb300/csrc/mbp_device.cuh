@@ -586,7 +586,8 @@ struct VnView {
   const M* lp;           // the tile's L_P (general inputs), lane
   const uint32_t* yt;    // the tile's sign words (BSC inputs) or NULL
   M ym;                  // this lane's ln((1 - e)/e) with yt
-  uint32_t* xh;          // the tile's decision words
+  uint32_t* xh;          // the tile's decision words (node-major: node i at xh[i * nt])
+  int nt;                // tiles of the decode
   uint32_t act;
 };
 
@@ -594,7 +595,7 @@ template <typename M, typename S, int POL>
 __device__ __forceinline__ VnView<M, S> vn_view(const DevCode& c, int tile, uint32_t act, const S* __restrict__ c2v,
                                                 M* __restrict__ lv, const M* __restrict__ lp,
                                                 const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
-                                                uint32_t* __restrict__ xh) {
+                                                uint32_t* __restrict__ xh, int nt) {
   const int lane = threadIdx.x & 31;
   const int64_t node0 = int64_t(tile) * c.n * kLanes + lane;
   VnView<M, S> v;
@@ -605,7 +606,8 @@ __device__ __forceinline__ VnView<M, S> vn_view(const DevCode& c, int tile, uint
   v.lp = lp + node0;
   v.yt = yt ? yt + int64_t(tile) * c.n : nullptr;
   v.ym = yt ? ld_state<POL>(ymag + tile * kLanes + lane) : M(0);
-  v.xh = xh + int64_t(tile) * c.n;
+  v.xh = xh + tile;
+  v.nt = nt;
   v.act = act;
   return v;
 }
@@ -641,7 +643,7 @@ __device__ __forceinline__ void vn_class_nodes(const VnView<M, S>& v, const int3
     if ((v.act >> lane) & 1u) v.lv[int64_t(col[j]) * kLanes] = sum;
     const uint32_t hard = __ballot_sync(kFull, sum < M(0));
     if (lane == 0) {
-      uint32_t* px = v.xh + col[j];
+      uint32_t* px = v.xh + int64_t(col[j]) * v.nt;
       *px = v.act == kFull ? hard : (ld_state<POL>(px) & ~v.act) | (hard & v.act);
     }
   }
@@ -665,7 +667,7 @@ __device__ __forceinline__ void vn_core(const VnView<M, S>& v, int col, const in
   if ((v.act >> lane) & 1u) v.lv[int64_t(col) * kLanes] = sum;
   const uint32_t hard = __ballot_sync(kFull, sum < M(0));
   if (lane == 0) {  // retired lanes keep their decision
-    uint32_t* px = v.xh + col;
+    uint32_t* px = v.xh + int64_t(col) * v.nt;
     *px = v.act == kFull ? hard : (ld_state<POL>(px) & ~v.act) | (hard & v.act);
   }
 }
@@ -684,18 +686,19 @@ template <typename M, typename S, int POL>
 __device__ __forceinline__ void vn_node(const DevCode& c, int tile, int col, uint32_t act,
                                         const S* __restrict__ c2v, M* __restrict__ lv, const M* __restrict__ lp,
                                         const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
-                                        uint32_t* __restrict__ xh) {
-  vn_view_node<M, S, POL>(vn_view<M, S, POL>(c, tile, act, c2v, lv, lp, yt, ymag, xh), col);
+                                        uint32_t* __restrict__ xh, int nt) {
+  vn_view_node<M, S, POL>(vn_view<M, S, POL>(c, tile, act, c2v, lv, lp, yt, ymag, xh, nt), col);
 }
 
 // ------------------------------------------------------- stopping rule
 
 // Rows r0 .. r0 + 31 of one tile, one per thread of a warp: the lanes whose hard
 // decision breaks the row are ORed into fail[tile][l] (l = the row's matrix).
-// The row's columns are all loaded before the decision words are gathered.
+// The row's columns are all loaded before the decision words (node-major, nt
+// tiles) are gathered.
 template <int DMAX, int POL>
 __device__ __forceinline__ void syn_rows(const DevCode& c, int tile, int r0, uint32_t act,
-                                         const uint32_t* __restrict__ xh, const uint32_t* __restrict__ zt,
+                                         const uint32_t* __restrict__ xh, int nt, const uint32_t* __restrict__ zt,
                                          uint32_t* __restrict__ fail) {
   const int r = r0 + (threadIdx.x & 31);
   uint32_t bad = 0;
@@ -707,11 +710,11 @@ __device__ __forceinline__ void syn_rows(const DevCode& c, int tile, int r0, uin
     int col[DMAX];
 #pragma unroll
     for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(cp + k) : -1;
-    const uint32_t* x = xh + int64_t(tile) * c.n;
+    const uint32_t* x = xh + tile;
     uint32_t p = zt[int64_t(tile) * c.m_tot + r];
 #pragma unroll
     for (int k = 0; k < DMAX; ++k)
-      if (col[k] >= 0) p ^= ld_state<POL>(x + col[k]);
+      if (col[k] >= 0) p ^= ld_state<POL>(x + int64_t(col[k]) * nt);
     bad = p & act;
     l = c.row_mat[r];
   }

@@ -85,8 +85,10 @@ struct DevState {
   uint32_t* yt;       // [n_tiles][n] Bob's bits, bit lane, for BSC inputs; NULL when L_P comes from lp
   void* chan_mag;     // [n_tiles][kLanes] ln((1 - e)/e) per frame (internal unit) for BSC inputs
   int32_t* lacc;      // [n_tiles][n][kLanes] fixed-point sum of C2V per node (FP32 single pass), or NULL
-  uint32_t* xh;       // [n_tiles][n] hard decisions, bit lane
+  uint32_t* xh;       // [n][n_tiles] hard decisions, bit lane (node-major: a node's words of 32 tiles are
+                      // one 128-byte line, which the stopping test reads per edge)
   uint32_t* zt;       // [n_tiles][m_tot] syndrome bits, bit lane
+  uint32_t* ztt;      // [m_tot][n_tiles] the same words row-major, for the streaming stopping test
   uint32_t* active;   // [n_tiles] lanes still decoding
   uint32_t* fail;     // [n_tiles][u] lanes whose hard decision violates some check of H_l
   int32_t* counters;  // [4]: unfinished tiles, non-finite flag

@@ -110,7 +110,7 @@ __global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restr
     const int i = w * 32 + b;
     if (lane == b && i < c.n) {
       yt[int64_t(tile) * c.n + i] = word;
-      xh[int64_t(tile) * c.n + i] = word & pos;
+      xh[int64_t(i) * gridDim.y + tile] = word & pos;
     }
   }
 }
@@ -133,12 +133,12 @@ __global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr
   }
   lp[(int64_t(tile) * c.n + col) * kLanes + lane] = v;
   const uint32_t hard = __ballot_sync(kFull, f < F && v < M(0));
-  if (lane == 0) xh[int64_t(tile) * c.n + col] = hard;
+  if (lane == 0) xh[int64_t(col) * gridDim.y + tile] = hard;
 }
 
 // Alice's syndrome bits, one word per (tile, check row in degree order) with bit = lane.
 __global__ void init_z_kernel(const DevCode c, int F, int n_tiles, const uint32_t* __restrict__ z,
-                              uint32_t* __restrict__ zt) {
+                              uint32_t* __restrict__ zt, uint32_t* __restrict__ ztt) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= int64_t(n_tiles) * c.m_tot) return;
   const int tile = int(idx / c.m_tot), r = int(idx % c.m_tot);
@@ -153,6 +153,7 @@ __global__ void init_z_kernel(const DevCode c, int F, int n_tiles, const uint32_
     if (f < F) word |= ((z[off + int64_t(f) * wl + (j >> 5)] >> (j & 31)) & 1u) << lane;
   }
   zt[idx] = word;
+  ztt[int64_t(r) * n_tiles + tile] = word;
 }
 
 __global__ void init_tiles_kernel(int F, int n_tiles, int u, uint32_t* __restrict__ active,
@@ -176,7 +177,7 @@ __global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restri
   if (w >= wn) return;
   const int lane = threadIdx.x & 31;
   const int i = w * 32 + lane;
-  const uint32_t word = i < c.n ? xh[int64_t(tile) * c.n + i] : 0u;
+  const uint32_t word = i < c.n ? xh[int64_t(i) * gridDim.y + tile] : 0u;
   for (int b = 0; b < kLanes; ++b) {
     const uint32_t bits = __ballot_sync(kFull, (word >> b) & 1u);
     const int f = tile * kLanes + b;
@@ -251,7 +252,7 @@ int setup_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s)
                                                                    a.validate);
     CKL("init_lp_kernel");
   }
-  init_z_kernel<<<blocks_for(int64_t(NT) * c.m_tot, 256), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt);
+  init_z_kernel<<<blocks_for(int64_t(NT) * c.m_tot, 256), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt, st.ztt);
   CKL("init_z_kernel");
   init_tiles_kernel<<<blocks_for(NT, 256), 256, 0, s>>>(F, NT, c.u, st.active, st.fail);
   CKL("init_tiles_kernel");
@@ -329,7 +330,7 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
 #undef CK
 }
 
-constexpr int kRegions = 20;
+constexpr int kRegions = 21;
 
 // bytes of one stored message and of one posterior / channel value
 size_t msg_size(int msg_dtype) {
@@ -366,6 +367,7 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
       NT * size_t(c.n) * 4,                                           // yt
       NT * size_t(kMaxRowDeg) * kLanes * node_size(msg_dtype),        // fmag
       NT * size_t(c.m_tot) * 4,                                       // rsgn
+      NT * size_t(c.m_tot) * 4,                                       // ztt
   };
   size_t t = 0;
   for (int i = 0; i < kRegions; ++i) {
@@ -422,6 +424,7 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->yt = reinterpret_cast<uint32_t*>(b + o[17]);
   st->fmag = b + o[18];
   st->rsgn = reinterpret_cast<uint32_t*>(b + o[19]);
+  st->ztt = reinterpret_cast<uint32_t*>(b + o[20]);
   st->counters = reinterpret_cast<int32_t*>(b + o[9]);
   st->ctl = b + o[10];
   st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256, 6) vn_multi_kernel(const MultiGroup* __re
       const int tile = gt - G.tile_base;
       v = vn_view<float, S, kPolStream>(G.c, tile, G.st.active[tile], static_cast<const S*>(G.st.c2v),
                                         static_cast<float*>(G.st.lv), static_cast<const float*>(G.st.lp), G.st.yt,
-                                        static_cast<const float*>(G.st.chan_mag), G.st.xh);
+                                        static_cast<const float*>(G.st.chan_mag), G.st.xh, G.st.n_tiles);
     }
     vn_view_node<float, S, kPolStream>(v, int(r - node0));
   }
@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(512) syn_multi_kernel(const MultiGroup* __rest
     const MultiGroup& G = gr[__ldg(tile_group + gt)];
     const int tile = gt - G.tile_base;
     const uint32_t act = G.st.active[tile];
-    syn_rows<DMAX, kPolStream>(G.c, tile, int(r - __ldg(pre + e)) * 32, act, G.st.xh, G.st.zt, G.st.fail);
+    syn_rows<DMAX, kPolStream>(G.c, tile, int(r - __ldg(pre + e)) * 32, act, G.st.xh, G.st.n_tiles, G.st.zt,
+                               G.st.fail);
   }
 }
 

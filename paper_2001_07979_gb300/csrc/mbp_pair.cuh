@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
       if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
       const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);
       if (lane == 0) {
-        uint32_t* px = xh + n0 + v;
+        uint32_t* px = xh + int64_t(v) * n_tiles + t.t0;
         *px = t.a0 == kFull ? hard : (__ldg(px) & ~t.a0) | (hard & t.a0);
       }
     }
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
       if (t.s1) lv[(n1 + v) * kLanes + lane] = sum1;
       const uint32_t hard = __ballot_sync(kFull, sum1 < 0.f);
       if (lane == 1) {
-        uint32_t* px = xh + n1 + v;
+        uint32_t* px = xh + int64_t(v) * n_tiles + t.t1;
         *px = t.a1 == kFull ? hard : (__ldg(px) & ~t.a1) | (hard & t.a1);
       }
     }
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int 
       if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
       const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);
       if (lane == 0) {
-        uint32_t* px = xh + n0 + v;
+        uint32_t* px = xh + int64_t(v) * n_tiles + t.t0;
         *px = t.a0 == kFull ? hard : (__ldg(px) & ~t.a0) | (hard & t.a0);
       }
     }
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int 
       if (t.s1) lv[(n1 + v) * kLanes + lane] = sum1;
       const uint32_t hard = __ballot_sync(kFull, sum1 < 0.f);
       if (lane == 1) {
-        uint32_t* px = xh + n1 + v;
+        uint32_t* px = xh + int64_t(v) * n_tiles + t.t1;
         *px = t.a1 == kFull ? hard : (__ldg(px) & ~t.a1) | (hard & t.a1);
       }
     }
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
       if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;
       const uint32_t hard = __ballot_sync(kFull, sum0 < 0.f);
       if (lane == 0) {
-        uint32_t* px = xh + n0 + v;
+        uint32_t* px = xh + int64_t(v) * n_tiles + t.t0;
         *px = t.a0 == kFull ? hard : (__ldg(px) & ~t.a0) | (hard & t.a0);
       }
     }
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
       if (t.s1) lv[(n1 + v) * kLanes + lane] = sum1;
       const uint32_t hard = __ballot_sync(kFull, sum1 < 0.f);
       if (lane == 1) {
-        uint32_t* px = xh + n1 + v;
+        uint32_t* px = xh + int64_t(v) * n_tiles + t.t1;
         *px = t.a1 == kFull ? hard : (__ldg(px) & ~t.a1) | (hard & t.a1);
       }
     }

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
     for (int it = gw; it < gt * row_groups; it += warps) {
       const int tile = g0 + it / row_groups;
       const uint32_t act = __ldcg(active + tile);
-      if (act) syn_rows<DMAX, kPolCoherent>(c, tile, (it % row_groups) * 32, act, xh, zt, fail);
+      if (act) syn_rows<DMAX, kPolCoherent>(c, tile, (it % row_groups) * 32, act, xh, n_tiles, zt, fail);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
       for (int it = gw; it < gt * c.n; it += warps) {
         const int tile = g0 + it / c.n;
         const uint32_t act = __ldcg(active + tile);
-        if (act) vn_node<M, M, kPolCoherent>(c, tile, it % c.n, act, c2v, lv, lp, yt, ymag, xh);
+        if (act) vn_node<M, M, kPolCoherent>(c, tile, it % c.n, act, c2v, lv, lp, yt, ymag, xh, n_tiles);
       }
       if (!grid_sync(ctl, gen, bc)) return;
       if (early_exit || t == max_iter) {

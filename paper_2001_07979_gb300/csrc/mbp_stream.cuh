@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __res
   if (act == 0) return;
   const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= c.n) return;
-  vn_node<M, S, kPolStream>(c, tile, col, act, c2v, lv, lp, yt, ymag, xh);
+  vn_node<M, S, kPolStream>(c, tile, col, act, c2v, lv, lp, yt, ymag, xh, gridDim.y);
 }
 
 // The same update for the nodes of one degree class (DevCode::vclass_*): a
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) vn_class_kernel(const DevCode c, int cls,
   const int qq = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
   if (qq >= count) return;
   const int d = c.vclass_deg[cls];
-  const VnView<M, S> v = vn_view<M, S, kPolStream>(c, tile, act, c2v, lv, lp, yt, ymag, xh);
+  const VnView<M, S> v = vn_view<M, S, kPolStream>(c, tile, act, c2v, lv, lp, yt, ymag, xh, gridDim.y);
   const int32_t* slots = c.vslot + c.vclass_toff[cls] + int64_t(qq) * d;
   if constexpr (D > 16) {  // long nodes: one per warp, 16 edges at a time
     vn_core<M, S, kPolStream>(v, __ldg(c.vnode + first + qq), slots, d);
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) vn_rows_kernel(const DevCode c, int cls, 
     if ((act >> lane) & 1u) lv[(node0 + col) * kLanes + lane] = sum;
     const uint32_t hard = __ballot_sync(kFull, sum < M(0));
     if (lane == 0) {
-      uint32_t* px = xh + node0 + col;
+      uint32_t* px = xh + int64_t(col) * gridDim.y + tile;
       *px = act == kFull ? hard : (__ldg(px) & ~act) | (hard & act);
     }
   }
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) vn_rows4_kernel(const DevCode c, int cls,
     if ((act >> lane) & 1u) lv[(node0 + col) * kLanes + lane] = sum;
     const uint32_t hard = __ballot_sync(kFull, sum < M(0));
     if (lane == 0) {
-      uint32_t* px = xh + node0 + col;
+      uint32_t* px = xh + int64_t(col) * gridDim.y + tile;
       *px = act == kFull ? hard : (__ldg(px) & ~act) | (hard & act);
     }
   }
@@ -410,20 +410,67 @@ __global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const in
   if ((act >> lane) & 1u) lv[at] = sum;
   const uint32_t hard = __ballot_sync(kFull, sum < M(0));
   if (lane == 0) {
-    uint32_t* px = xh + int64_t(tile) * c.n + col;
+    uint32_t* px = xh + int64_t(col) * gridDim.y + tile;
     *px = (*px & ~act) | (hard & act);
   }
 }
 
-// One thread per (tile, check row).
+// The stopping test (the node-major decision words, DevState::xh): a warp takes kSynRows
+// consecutive check rows (in position order, so one matrix except where the
+// matrices meet) for 32 tiles, lane = tile (tiles 32 y .. 32 y + 31, y =
+// blockIdx.y): every edge's words for those tiles are one coalesced line. The
+// failing lanes of each tile are ORed over the warp's rows and then into
+// fail[tile][l], once per matrix met.
+constexpr int kSynRows = 8;
+
 template <int DMAX>
-__global__ void __launch_bounds__(256) syn_kernel(const DevCode c, const uint32_t* __restrict__ xh,
-                                                  const uint32_t* __restrict__ zt,
+__global__ void __launch_bounds__(256) syn_kernel(const DevCode c, int n_tiles, const uint32_t* __restrict__ xh,
+                                                  const uint32_t* __restrict__ ztt,
                                                   const uint32_t* __restrict__ active, uint32_t* __restrict__ fail) {
-  const int tile = blockIdx.y;
-  const uint32_t act = active[tile];
-  if (act == 0) return;
-  syn_rows<DMAX, kPolStream>(c, tile, blockIdx.x * blockDim.x + (threadIdx.x & ~31), act, xh, zt, fail);
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.y * kLanes + lane;
+  const bool tv = tile < n_tiles;
+  const uint32_t act = tv ? active[tile] : 0u;
+  if (__ballot_sync(kFull, act != 0) == 0) return;
+  const int r0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * kSynRows;
+  if (r0 >= c.m_tot) return;
+  uint32_t acc = 0;
+  int lcur = c.row_mat[r0];
+#pragma unroll
+  for (int i = 0; i < kSynRows; ++i) {
+    const int r = r0 + i;
+    if (r >= c.m_tot) break;
+    const int l = c.row_mat[r];
+    if (l != lcur) {  // warp-uniform
+      if (acc) atomicOr(&fail[tile * c.u + lcur], acc);
+      acc = 0;
+      lcur = l;
+    }
+    const int base = c.slice_base[r];
+    const int deg = c.slice_base[r + 1] - base;
+    int col[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(c.slot_col + base + k) : -1;
+    uint32_t w = tv ? __ldg(ztt + int64_t(r) * n_tiles + tile) : 0u;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (col[k] >= 0 && tv) w ^= __ldg(xh + int64_t(col[k]) * n_tiles + tile);
+    acc |= w & act;
+  }
+  if (acc) atomicOr(&fail[tile * c.u + lcur], acc);
+}
+
+template <int DMAX>
+void launch_syn(const DevCode& c, const DevState& st, cudaStream_t s) {
+  const dim3 grid(blocks_for(c.m_tot, 8 * kSynRows), unsigned((st.n_tiles + kLanes - 1) / kLanes));
+  syn_kernel<DMAX><<<grid, 256, 0, s>>>(c, st.n_tiles, st.xh, st.ztt, st.active, st.fail);
+}
+
+inline void launch_syn_any(const DevCode& c, const DevState& st, cudaStream_t s) {
+  if (c.max_row_deg <= 8) launch_syn<8>(c, st, s);
+  else if (c.max_row_deg <= 16) launch_syn<16>(c, st, s);
+  else if (c.max_row_deg <= 32) launch_syn<32>(c, st, s);
+  else launch_syn<kMaxRowDeg>(c, st, s);
 }
 
 // One thread per tile.
@@ -548,10 +595,9 @@ void launch_cn_any(const DevCode& c, const DevState& st, const CnLaunch& q, doub
 // One flooding sum-product iteration of one group without any host synchronisation (the grid kernels of the
 // grouped decode): eq. (6) over every row, eq. (2) and the hard decision, and the stopping test; the caller
 // retires the finished frames.
-template <typename M, typename S>
 // iter: 1, 2, or 0 for any later iteration (iterations 1 and 2 differ in where their messages come from).
+template <typename M, typename S>
 cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s) {
-  const int NT = st.n_tiles;
   const bool rows = rows_ok(c, st);
   const CnLaunch q{0, c.m_tot, iter == 1, iter == 1 ? st.lp : st.lv, st.yt, rows ? (iter == 1 || iter == 2 ? iter : 0) : 0};
   const int fam = q.rows ? MBP_KERNEL_CHECK_ROWS : MBP_KERNEL_CHECK;
@@ -565,11 +611,7 @@ cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_end(MBP_KERNEL_VARIABLE, s, c.n_vclass > 0 ? c.n_vclass : 1);
   prof_begin(MBP_KERNEL_SYNDROME, s);
-  const dim3 syn_grid(blocks_for(c.m_tot, 256), NT);
-  if (c.max_row_deg <= 8) syn_kernel<8><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
-  else if (c.max_row_deg <= 16) syn_kernel<16><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
-  else if (c.max_row_deg <= 32) syn_kernel<32><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
-  else syn_kernel<kMaxRowDeg><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+  launch_syn_any(c, st, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_end(MBP_KERNEL_SYNDROME, s, 1);
   return cudaSuccess;
@@ -583,15 +625,11 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
   if ((e = (call)) != cudaSuccess) return cuda_error(e, what)
 #define CKL(what) CK(cudaGetLastError(), what)
   const int F = st.F, NT = st.n_tiles;
-  const dim3 syn_grid(blocks_for(c.m_tot, 256), NT);
   const dim3 node_grid(blocks_for(c.n, 8), NT);
   int32_t host_ctr[1];
   auto stop_check = [&](int t, int* left) -> int {
     prof_begin(MBP_KERNEL_SYNDROME, s);
-    if (c.max_row_deg <= 8) syn_kernel<8><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
-    else if (c.max_row_deg <= 16) syn_kernel<16><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
-    else if (c.max_row_deg <= 32) syn_kernel<32><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
-    else syn_kernel<kMaxRowDeg><<<syn_grid, 256, 0, s>>>(c, st.xh, st.zt, st.active, st.fail);
+    launch_syn_any(c, st, s);
     CKL("syn_kernel");
     prof_end(MBP_KERNEL_SYNDROME, s, 1);
     CK(cudaMemsetAsync(st.counters, 0, sizeof(int32_t), s), "clear counter");
