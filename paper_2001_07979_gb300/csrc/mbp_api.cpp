@@ -301,13 +301,14 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   });
   for (int l = 0; l <= u; ++l) d.row_pos[l] = d.row_first[l];  // matrices stay in stacked order
   std::vector<uint8_t> perm_mat(std::max<int64_t>(m_tot, 1));
-  std::vector<int32_t> perm_local(std::max<int64_t>(m_tot, 1));
+  std::vector<int32_t> perm_local(std::max<int64_t>(m_tot, 1)), row_at(std::max<int64_t>(m_tot, 1));
   std::vector<int32_t> slice_base(m_tot + 1);
   slice_base[0] = 0;
   for (int64_t p = 0; p < m_tot; ++p) {
     const int32_t r = order[p];
     perm_mat[p] = row_mat[r];
     perm_local[p] = r - d.row_first[row_mat[r]];
+    row_at[r] = int32_t(p);
     slice_base[p + 1] = slice_base[p] + row_deg[r];
   }
   d.s_tot = slice_base[m_tot];
@@ -374,7 +375,8 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
       {row_ptr.data(), row_ptr.size() * 4, 0},       {col_idx.data(), col_idx.size() * 4, 0},
       {edge_slot.data(), edge_slot.size() * 4, 0},   {perm_mat.data(), perm_mat.size(), 0},
       {perm_local.data(), perm_local.size() * 4, 0}, {vnode.data(), vnode.size() * 4, 0},
-      {vslot.data(), vslot.size() * 4, 0},           {vrow.data(), vrow.size() * 4, 0}};
+      {vslot.data(), vslot.size() * 4, 0},           {vrow.data(), vrow.size() * 4, 0},
+      {row_at.data(), row_at.size() * 4, 0}};
   size_t total = 0;
   for (auto& p : parts) {
     p.off = total;
@@ -413,6 +415,7 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   d.vslot = reinterpret_cast<const int32_t*>(base + parts[10].off);
   // the packed row table holds positions below 2^25; larger codes keep iteration 1 per edge
   d.vrow = m_tot < (int64_t(1) << 25) ? reinterpret_cast<const int32_t*>(base + parts[11].off) : nullptr;
+  d.row_at = reinterpret_cast<const int32_t*>(base + parts[12].off);
   h->d = d;
   *out = h;
   return MBP_OK;

@@ -63,6 +63,7 @@ struct DevCode {
   const int32_t* edge_slot;   // [e_tot] stacked CSR edge -> slot
   const uint8_t* row_mat;     // [m_tot] matrix l of the row at position p
   const int32_t* row_local;   // [m_tot] row index j inside H_l of the row at position p
+  const int32_t* row_at;      // [m_tot] the position of stacked row r (the inverse of the two above)
   // Variable nodes grouped by their degree over all matrices (n_vclass = 0 when there are more classes than
   // kMaxVClasses): class k holds node positions vclass_first[k] .. vclass_first[k+1] - 1, all of degree
   // vclass_deg[k]; vnode gives the node at each position, and the class's slots (col_slot order, one row of
@@ -167,7 +168,9 @@ int static_scratch(void** ptr);
 template <typename M, typename S>
 int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double l_max, float qscale,
                       float inv_qscale, cudaStream_t s);
-// one flooding iteration of one group, no host synchronisation (grouped decode; float arithmetic)
+// one flooding iteration of one group, no host synchronisation (grouped decode; float arithmetic); iter = 1,
+// 2, 0 for a later iteration, or kStopTestOnly for the stopping test before iteration 1 alone
+constexpr int kStopTestOnly = -1;
 template <typename M, typename S>
 cudaError_t stream_group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s);
 template <typename M>

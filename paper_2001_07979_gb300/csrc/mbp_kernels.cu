@@ -93,7 +93,8 @@ __global__ void chan_mag_kernel(const double* __restrict__ qber, int F, int n_la
 // BSC inputs: Bob's bits into one word per (tile, node) with bit = lane (the
 // sign words of L_P = (1 - 2y) mag, eq. 5), and the hard decision of iteration
 // 0, [L_P < 0] = y where mag > 0. One warp per (tile, 32-node word): lane l
-// reads frame l's word, and a ballot per node transposes it.
+// reads frame l's word, and a warp bit transpose gives lane b node 32 w + b's
+// word.
 template <typename M>
 __global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ y, const M* __restrict__ mag,
                                  uint32_t* __restrict__ yt, uint32_t* __restrict__ xh) {
@@ -105,13 +106,11 @@ __global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restr
   const int f = tile * kLanes + lane;
   const uint32_t yw = f < F ? y[int64_t(f) * wn + w] : 0u;
   const uint32_t pos = __ballot_sync(kFull, mag[tile * kLanes + lane] > M(0));
-  for (int b = 0; b < 32; ++b) {
-    const uint32_t word = __ballot_sync(kFull, (yw >> b) & 1u);
-    const int i = w * 32 + b;
-    if (lane == b && i < c.n) {
-      yt[int64_t(tile) * c.n + i] = word;
-      xh[int64_t(i) * gridDim.y + tile] = word & pos;
-    }
+  const uint32_t word = warp_transpose32(yw);  // lane b: node 32 w + b, bit = frame
+  const int i = w * 32 + lane;
+  if (i < c.n) {
+    yt[int64_t(tile) * c.n + i] = word;
+    xh[int64_t(i) * gridDim.y + tile] = word & pos;
   }
 }
 
@@ -136,24 +135,33 @@ __global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr
   if (lane == 0) xh[int64_t(col) * gridDim.y + tile] = hard;
 }
 
-// Alice's syndrome bits, one word per (tile, check row in degree order) with bit = lane.
+// Alice's syndrome bits into one word per (tile, check row in degree order) with
+// bit = lane, tile-major (zt) and row-major (ztt). One warp per (tile, 32-row
+// word of one matrix): lane f reads frame f's word, and a warp bit transpose
+// gives lane b the word of row 32 g + b of H_l.
 __global__ void init_z_kernel(const DevCode c, int F, int n_tiles, const uint32_t* __restrict__ z,
                               uint32_t* __restrict__ zt, uint32_t* __restrict__ ztt) {
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= int64_t(n_tiles) * c.m_tot) return;
-  const int tile = int(idx / c.m_tot), r = int(idx % c.m_tot);
-  const int l = c.row_mat[r];
-  const int j = c.row_local[r];
+  const int tile = blockIdx.y;
+  int g = blockIdx.x * 8 + (threadIdx.x >> 5);  // word over all matrices, then within H_l
+  int l = 0;
   int64_t off = 0;
-  for (int q = 0; q < l; ++q) off += int64_t(F) * ((c.m[q] + 31) >> 5);
-  const int wl = (c.m[l] + 31) >> 5;
-  uint32_t word = 0;
-  for (int lane = 0; lane < kLanes; ++lane) {
-    const int f = tile * kLanes + lane;
-    if (f < F) word |= ((z[off + int64_t(f) * wl + (j >> 5)] >> (j & 31)) & 1u) << lane;
+  while (l < c.u && g >= ((c.m[l] + 31) >> 5)) {
+    const int wl = (c.m[l] + 31) >> 5;
+    g -= wl;
+    off += int64_t(F) * wl;
+    ++l;
   }
-  zt[idx] = word;
-  ztt[int64_t(r) * n_tiles + tile] = word;
+  if (l >= c.u) return;
+  const int wl = (c.m[l] + 31) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int f = tile * kLanes + lane;
+  const uint32_t word = warp_transpose32(f < F ? z[off + int64_t(f) * wl + g] : 0u);
+  const int j = g * 32 + lane;
+  if (j < c.m[l]) {
+    const int p = c.row_at[c.row_first[l] + j];
+    zt[int64_t(tile) * c.m_tot + p] = word;
+    ztt[int64_t(p) * n_tiles + tile] = word;
+  }
 }
 
 __global__ void init_tiles_kernel(int F, int n_tiles, int u, uint32_t* __restrict__ active,
@@ -168,8 +176,7 @@ __global__ void init_tiles_kernel(int F, int n_tiles, int u, uint32_t* __restric
 // ------------------------------------------------------------- outputs
 
 // One warp per (tile, 32-node word): lane i reads node 32 w + i's decision word
-// (one bit per frame); a ballot per frame transposes it into that frame's
-// output word.
+// (one bit per frame); a warp bit transpose gives lane f frame f's output word.
 __global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ xh, uint32_t* __restrict__ out) {
   const int wn = (c.n + 31) >> 5;
   const int tile = blockIdx.y;
@@ -178,11 +185,9 @@ __global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restri
   const int lane = threadIdx.x & 31;
   const int i = w * 32 + lane;
   const uint32_t word = i < c.n ? xh[int64_t(i) * gridDim.y + tile] : 0u;
-  for (int b = 0; b < kLanes; ++b) {
-    const uint32_t bits = __ballot_sync(kFull, (word >> b) & 1u);
-    const int f = tile * kLanes + b;
-    if (lane == b && f < F) out[int64_t(f) * wn + w] = bits;
-  }
+  const uint32_t bits = warp_transpose32(word);  // lane f: frame f's bits of nodes 32 w .. 32 w + 31
+  const int f = tile * kLanes + lane;
+  if (f < F) out[int64_t(f) * wn + w] = bits;
 }
 
 template <typename M>
@@ -252,7 +257,10 @@ int setup_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s)
                                                                    a.validate);
     CKL("init_lp_kernel");
   }
-  init_z_kernel<<<blocks_for(int64_t(NT) * c.m_tot, 256), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt, st.ztt);
+  int zwords = 0;
+  for (int l = 0; l < c.u; ++l) zwords += (c.m[l] + 31) >> 5;
+  if (zwords > 0)
+    init_z_kernel<<<dim3(blocks_for(zwords, 8), NT), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt, st.ztt);
   CKL("init_z_kernel");
   init_tiles_kernel<<<blocks_for(NT, 256), 256, 0, s>>>(F, NT, c.u, st.active, st.fail);
   CKL("init_tiles_kernel");

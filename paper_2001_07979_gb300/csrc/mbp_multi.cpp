@@ -136,10 +136,19 @@ Kernels kernels_of(int msg_dtype) {
 
 const GroupConds kNoConds{0, {}};
 
-// The test before iteration 1 (lists of every tile, syndrome test, retirement at t = 0).
+// The test before iteration 1 and the retirement at t = 0: persistent kernels build the lists of every tile
+// and run the class syndrome kernels over them; grid kernels run each group's stopping test.
 cudaError_t issue_prologue(const Kernels& k, const MultiTables& tb, const MultiShape& sh, const MultiTuning& tu,
-                           int sms, int in_graph, unsigned long long h, const GroupConds& gc, cudaStream_t s) {
+                           int sms, const Groups& gs, int in_graph, unsigned long long h, const GroupConds& gc,
+                           cudaStream_t s) {
   cudaError_t e;
+  if (tu.grid) {
+    for (size_t g = 0; g < gs.code.size(); ++g) {
+      if (gs.st[g].F == 0) continue;
+      if ((e = k.group_step(gs.code[g], gs.st[g], kStopTestOnly, gs.l_max, s)) != cudaSuccess) return e;
+    }
+    return k.build_lists(tb, sh, 2, in_graph, h, gc, s);
+  }
   if ((e = k.build_lists(tb, sh, 0, 0, 0, kNoConds, s)) != cudaSuccess) return e;
   for (int c = 0; c < sh.n_cls; ++c)
     if ((e = k.syndrome(tb, sh, c, tu, sms, s)) != cudaSuccess) return e;
@@ -271,7 +280,7 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
         gb.h[q] = hb;
       }
     }
-    GR(capture_after(g, {}, cs, [&](cudaStream_t st) { return issue_prologue(k, tb, sh, tu, sms, 1, h, ga, st); },
+    GR(capture_after(g, {}, cs, [&](cudaStream_t st) { return issue_prologue(k, tb, sh, tu, sms, gs, 1, h, ga, st); },
                      &leaf, "capture (prologue)"));
     if (tu.grid) {  // iterations 1 and 2
       branches.clear();
@@ -494,9 +503,14 @@ int run_multi(const mbp_group* g, int G, int max_iter, const mbp_opts* o, bool h
     // host-driven loop: the same kernels, one launch each, with a read-back of the loop condition
     int32_t cond = 0;
     prof_begin(MBP_KERNEL_RETIRE, s);
-    if ((e = issue_prologue(k, tb, sh, tu, sms, 0, 0, kNoConds, s)) != cudaSuccess)
+    if ((e = issue_prologue(k, tb, sh, tu, sms, gs, 0, 0, kNoConds, s)) != cudaSuccess)
       return cuda_error(e, "grouped prologue");
-    prof_end(MBP_KERNEL_RETIRE, s, 2 + sh.n_cls);
+    int pro = 2 + sh.n_cls;
+    if (tu.grid) {
+      pro = 1;
+      for (const auto& q : gs.st) pro += q.F > 0;
+    }
+    prof_end(MBP_KERNEL_RETIRE, s, pro);
     for (int t = 1;; ++t) {
       if ((e = cudaMemcpyAsync(&cond, &tb.ctl->cond, sizeof cond, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_error(e, "read loop condition");

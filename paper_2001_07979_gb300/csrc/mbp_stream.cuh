@@ -595,9 +595,14 @@ void launch_cn_any(const DevCode& c, const DevState& st, const CnLaunch& q, doub
 // One flooding sum-product iteration of one group without any host synchronisation (the grid kernels of the
 // grouped decode): eq. (6) over every row, eq. (2) and the hard decision, and the stopping test; the caller
 // retires the finished frames.
-// iter: 1, 2, or 0 for any later iteration (iterations 1 and 2 differ in where their messages come from).
+// iter: 1, 2, or 0 for any later iteration (iterations 1 and 2 differ in where their messages come from);
+// kStopTestOnly: the stopping test before iteration 1.
 template <typename M, typename S>
 cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s) {
+  if (iter == kStopTestOnly) {
+    launch_syn_any(c, st, s);
+    return cudaGetLastError();
+  }
   const bool rows = rows_ok(c, st);
   const CnLaunch q{0, c.m_tot, iter == 1, iter == 1 ? st.lp : st.lv, st.yt, rows ? (iter == 1 || iter == 2 ? iter : 0) : 0};
   const int fam = q.rows ? MBP_KERNEL_CHECK_ROWS : MBP_KERNEL_CHECK;
