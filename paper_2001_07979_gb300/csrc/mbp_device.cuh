@@ -482,9 +482,10 @@ struct CnView {
   int32_t* lacc;         // the tile's fixed-point sums, lane (FIXED) or NULL
   uint32_t act;          // lanes still decoding
   // iteration 2 after a row-form iteration 1 (else NULL): the tile's magnitude table (by row degree, lane),
-  // row sign words and Bob's sign words
+  // row sign words (row p at rs[p * rs_nt]) and Bob's sign words
   const M* rm;
   const uint32_t* rs;
+  int rs_nt;
   const uint32_t* yprev;
 };
 
@@ -508,6 +509,7 @@ __device__ __forceinline__ CnView<M, S> cn_view(const DevCode& c, int tile, uint
   v.act = act;
   v.rm = nullptr;
   v.rs = nullptr;
+  v.rs_nt = 0;
   v.yprev = nullptr;
   return v;
 }
@@ -524,7 +526,7 @@ __device__ __forceinline__ void cn_view_row(const CnView<M, S>& v, int p, int fi
   cn_tile_row_src<M, S, DMAX, FIXED, POL, RIN>(deg, v.slot_col + base, v.gsrc, v.ysrc, v.ym,
                                                v.msg + int64_t(base) * kMsgStride<S>, first_iter, par, store, l_max,
                                                d_lmax, v.lacc, qscale, RIN ? v.rm + (deg - 1) * kLanes : nullptr,
-                                               RIN ? v.rs + p : nullptr, v.yprev);
+                                               RIN ? v.rs + int64_t(p) * v.rs_nt : nullptr, v.yprev);
 }
 
 // Min-sum rule for check row p of the view's tile (FP32 arithmetic).

@@ -96,9 +96,10 @@ struct DevState {
   void* ctl;          // control block of the resident schedule (barrier, retirement)
   // Row form of the first iteration's messages (BSC inputs): the C2V of row p
   // (degree d) to a node is +-fmag[tile][d - 1][lane], with sign bit lane of
-  // rsgn[tile][p] ^ yt[tile][node]
+  // rsgn[p][tile] ^ yt[tile][node]
   void* fmag;         // [n_tiles][kMaxRowDeg][kLanes] arithmetic type (rounded to the message type)
-  uint32_t* rsgn;     // [n_tiles][m_tot]
+  uint32_t* rsgn;     // [m_tot][n_tiles] (row-major)
+  uint32_t* ppos;     // [n_tiles] the lanes whose channel magnitude ln((1 - e)/e) is positive (BSC inputs)
   // staging for mbp_decode_bsc_host
   uint32_t* io_y;
   double* io_qber;

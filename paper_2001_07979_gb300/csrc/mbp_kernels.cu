@@ -97,7 +97,7 @@ __global__ void chan_mag_kernel(const double* __restrict__ qber, int F, int n_la
 // word.
 template <typename M>
 __global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ y, const M* __restrict__ mag,
-                                 uint32_t* __restrict__ yt, uint32_t* __restrict__ xh) {
+                                 uint32_t* __restrict__ yt, uint32_t* __restrict__ xh, uint32_t* __restrict__ ppos) {
   const int wn = (c.n + 31) >> 5;
   const int tile = blockIdx.y;
   const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -106,6 +106,7 @@ __global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restr
   const int f = tile * kLanes + lane;
   const uint32_t yw = f < F ? y[int64_t(f) * wn + w] : 0u;
   const uint32_t pos = __ballot_sync(kFull, mag[tile * kLanes + lane] > M(0));
+  if (w == 0 && lane == 0) ppos[tile] = pos;
   const uint32_t word = warp_transpose32(yw);  // lane b: node 32 w + b, bit = frame
   const int i = w * 32 + lane;
   if (i < c.n) {
@@ -207,7 +208,7 @@ __global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv
 // row-form iteration 1 (flag counters[2]), rebuilt from the rows (row_msg).
 template <typename M, typename S>
 __global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, int frame, M* __restrict__ out,
-                                  const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn,
+                                  int n_tiles, const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn,
                                   const uint32_t* __restrict__ yt, const int32_t* __restrict__ counters) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= c.e_tot) return;
@@ -222,7 +223,7 @@ __global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, in
       else hi = mid;
     }
     const int deg = c.slice_base[lo + 1] - c.slice_base[lo];
-    v = row_msg(fmag[(int64_t(tile) * kMaxRowDeg + deg - 1) * kLanes + lane], rsgn[int64_t(tile) * c.m_tot + lo],
+    v = row_msg(fmag[(int64_t(tile) * kMaxRowDeg + deg - 1) * kLanes + lane], rsgn[int64_t(lo) * n_tiles + tile],
                 yt[int64_t(tile) * c.n + c.col_idx[e]], lane);
   } else {
     v = M(Store<S>::widen(c2v[msg_at<S>(tile, c.s_tot, lane) + int64_t(slot) * kMsgStride<S>]));
@@ -248,7 +249,7 @@ int setup_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s)
                                                                    static_cast<M*>(st.chan_mag));
     CKL("chan_mag_kernel");
     init_bits_kernel<M><<<dim3(blocks_for((c.n + 31) >> 5, 8), NT), 256, 0, s>>>(
-        c, F, a.y_bits, static_cast<const M*>(st.chan_mag), st.yt, st.xh);
+        c, F, a.y_bits, static_cast<const M*>(st.chan_mag), st.yt, st.xh, st.ppos);
     CKL("init_bits_kernel");
   } else {
     st.yt = nullptr;
@@ -338,7 +339,7 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
 #undef CK
 }
 
-constexpr int kRegions = 21;
+constexpr int kRegions = 22;
 
 // bytes of one stored message and of one posterior / channel value
 size_t msg_size(int msg_dtype) {
@@ -376,6 +377,7 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
       NT * size_t(kMaxRowDeg) * kLanes * node_size(msg_dtype),        // fmag
       NT * size_t(c.m_tot) * 4,                                       // rsgn
       NT * size_t(c.m_tot) * 4,                                       // ztt
+      NT * 4,                                                         // ppos
   };
   size_t t = 0;
   for (int i = 0; i < kRegions; ++i) {
@@ -433,6 +435,7 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->fmag = b + o[18];
   st->rsgn = reinterpret_cast<uint32_t*>(b + o[19]);
   st->ztt = reinterpret_cast<uint32_t*>(b + o[20]);
+  st->ppos = reinterpret_cast<uint32_t*>(b + o[21]);
   st->counters = reinterpret_cast<int32_t*>(b + o[9]);
   st->ctl = b + o[10];
   st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;
@@ -490,7 +493,7 @@ cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtyp
   const unsigned grid = blocks_for(c.e_tot, 256);
 #define MBP_EXPORT(M, S)                                                                                     \
   export_c2v_kernel<M, S><<<grid, 256, 0, s>>>(c, static_cast<const S*>(st.c2v), frame, static_cast<M*>(out), \
-                                               static_cast<const M*>(st.fmag), st.rsgn, st.yt, st.counters)
+                                               st.n_tiles, static_cast<const M*>(st.fmag), st.rsgn, st.yt, st.counters)
   if (msg_dtype == MBP_MSG_F64) MBP_EXPORT(double, double);
   else if (msg_dtype == MBP_MSG_F16) MBP_EXPORT(float, __half);
   else if (msg_dtype == MBP_MSG_BF16) MBP_EXPORT(float, __nv_bfloat16);

@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256, cn_pair_min_blocks(DMAX))
   const float inv = Arith<float>::delta(l_max);  // d_lmax
   PairRows rows;
   if constexpr (RIN) {
-    const int64_t r0 = int64_t(t.t0) * c.m_tot + p, r1 = int64_t(t.t1) * c.m_tot + p;
+    const int64_t r0 = int64_t(p) * n_tiles + t.t0, r1 = int64_t(p) * n_tiles + t.t1;
     rows.m0 = h0 ? __ldg(fmag + (int64_t(t.t0) * kMaxRowDeg + deg - 1) * kLanes + lane) : 0.f;
     rows.m1 = h1 ? __ldg(fmag + (int64_t(t.t1) * kMaxRowDeg + deg - 1) * kLanes + lane) : 0.f;
     rows.s0 = h0 ? __ldg(rsgn + r0) : 0u;
@@ -404,8 +404,8 @@ __global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int 
   const int cnt = min(N, count - q0);
   const bool on = lane < cnt * d;
   const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
-  const uint32_t rs0 = on && h0 ? __ldg(rsgn + int64_t(t.t0) * c.m_tot + (e >> 6)) : 0u;
-  const uint32_t rs1 = on && h1 ? __ldg(rsgn + int64_t(t.t1) * c.m_tot + (e >> 6)) : 0u;
+  const uint32_t rs0 = on && h0 ? __ldg(rsgn + int64_t(e >> 6) * n_tiles + t.t0) : 0u;
+  const uint32_t rs1 = on && h1 ? __ldg(rsgn + int64_t(e >> 6) * n_tiles + t.t1) : 0u;
   const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
   const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
   const uint32_t my0 = lane < cnt && h0 ? __ldg(yt + n0 + mycol) : 0u;
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
   const int cnt = min(N, count - q0);
   const bool on = lane < cnt * d;
   const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
-  const uint32_t T0 = warp_transpose32(on && h0 ? __ldg(rsgn + int64_t(t.t0) * c.m_tot + (e >> 6)) : 0u);
-  const uint32_t T1 = warp_transpose32(on && h1 ? __ldg(rsgn + int64_t(t.t1) * c.m_tot + (e >> 6)) : 0u);
+  const uint32_t T0 = warp_transpose32(on && h0 ? __ldg(rsgn + int64_t(e >> 6) * n_tiles + t.t0) : 0u);
+  const uint32_t T1 = warp_transpose32(on && h1 ? __ldg(rsgn + int64_t(e >> 6) * n_tiles + t.t1) : 0u);
   const int rel = on ? (e & 63) + 1 - c.min_row_deg : 0;  // 0 .. 2^NB - 1
   const uint32_t b0 = __ballot_sync(kFull, rel & 1), b1 = NB > 1 ? __ballot_sync(kFull, (rel >> 1) & 1) : 0u;
   const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;

@@ -28,6 +28,10 @@ using namespace dev;
 
 inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
+// Check rows per warp of the kernels that take rows with lane = tile (stopping
+// test, first-iteration row signs).
+constexpr int kSynRows = 8;
+
 // Resident blocks of 256 threads the check kernel is compiled for: 5 per SM (48
 // registers, no spills) for float rows of up to 14 edges, more latency hiding
 // than the 4 that 64 registers allow; longer rows (and FP64) keep the
@@ -61,7 +65,8 @@ __global__ void __launch_bounds__(256, cn_min_blocks<M>(DMAX)) cn_kernel(const D
                                              FIXED ? lacc : nullptr);
   if constexpr (RIN) {
     v.rm = fmag + int64_t(tile) * kMaxRowDeg * kLanes + (threadIdx.x & 31);
-    v.rs = rsgn + int64_t(tile) * c.m_tot;
+    v.rs = rsgn + tile;
+    v.rs_nt = gridDim.y;
     v.yprev = yt + int64_t(tile) * c.n;
   }
   cn_view_row<M, S, DMAX, FIXED, kPolStream, RIN>(v, p, first_iter, l_max, Arith<M>::delta(l_max), qscale);
@@ -95,28 +100,47 @@ __global__ void __launch_bounds__(256) cn_first_kernel(const DevCode c, int p0, 
 
 // Iteration 1 of BSC inputs in row form (DevState::fmag), part 1: the sign word of
 // each row, z_j xor the row's parity of Bob's bits, for the 32 frames of a tile at
-// once (one thread per (tile, row)); the kernel sets the row-form flag counters[2].
+// once. Before iteration 1's variable-node pass the decision words are Bob's bits
+// (node-major: one coalesced line per edge for 32 tiles) wherever the frame's
+// channel magnitude is positive; the bits of other frames come from yt. A warp
+// takes kSynRows rows, lane = tile, and writes the words row-major; the kernel
+// sets the row-form flag counters[2].
 template <int DMAX>
-__global__ void __launch_bounds__(256) first_rows_kernel(const DevCode c, const uint32_t* __restrict__ yt,
-                                                         const uint32_t* __restrict__ zt,
+__global__ void __launch_bounds__(256) first_rows_kernel(const DevCode c, int n_tiles, const uint32_t* __restrict__ xh,
+                                                         const uint32_t* __restrict__ ztt,
+                                                         const uint32_t* __restrict__ yt,
+                                                         const uint32_t* __restrict__ ppos,
                                                          const uint32_t* __restrict__ active,
                                                          uint32_t* __restrict__ rsgn, int32_t* __restrict__ counters) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[2] = 1;
-  const int tile = blockIdx.y;
-  if (active[tile] == 0) return;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= c.m_tot) return;
-  const int base = c.slice_base[p];
-  const int deg = c.slice_base[p + 1] - base;
-  int col[DMAX];
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.y * kLanes + lane;
+  const bool tv = tile < n_tiles;
+  const uint32_t act = tv ? active[tile] : 0u;
+  if (__ballot_sync(kFull, act != 0) == 0) return;
+  const int r0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * kSynRows;
+  if (r0 >= c.m_tot) return;
+  const uint32_t pp = tv ? ppos[tile] : kFull;
+  const uint32_t* y = yt + int64_t(tv ? tile : 0) * c.n;
 #pragma unroll
-  for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(c.slot_col + base + k) : -1;
-  const uint32_t* y = yt + int64_t(tile) * c.n;
-  uint32_t w = zt[int64_t(tile) * c.m_tot + p];
+  for (int i = 0; i < kSynRows; ++i) {
+    const int r = r0 + i;
+    if (r < c.m_tot) {
+      const int base = c.slice_base[r];
+      const int deg = c.slice_base[r + 1] - base;
+      uint32_t x = tv ? __ldg(ztt + int64_t(r) * n_tiles + tile) : 0u;
 #pragma unroll
-  for (int k = 0; k < DMAX; ++k)
-    if (col[k] >= 0) w ^= __ldg(y + col[k]);
-  rsgn[int64_t(tile) * c.m_tot + p] = w;
+      for (int k = 0; k < DMAX; ++k)
+        if (k < deg) {
+          const int col = __ldg(c.slot_col + base + k);
+          if (tv) {
+            x ^= __ldg(xh + int64_t(col) * n_tiles + tile);
+            if (pp != kFull) x ^= __ldg(y + col) & ~pp;
+          }
+        }
+      if (tv) rsgn[int64_t(r) * n_tiles + tile] = x;
+    }
+  }
 }
 
 // Part 2: the output magnitude of a row of degree d (the same for every row of
@@ -218,7 +242,7 @@ __global__ void __launch_bounds__(256) vn_rows_kernel(const DevCode c, int cls, 
   const int cnt = min(N, count - q0);
   const bool on = lane < cnt * d;
   const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
-  const uint32_t rs = on ? __ldg(rsgn + int64_t(tile) * c.m_tot + (e >> 6)) : 0u;
+  const uint32_t rs = on ? __ldg(rsgn + int64_t(e >> 6) * gridDim.y + tile) : 0u;
   const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
   const uint32_t myy = lane < cnt ? __ldg(yt + int64_t(tile) * c.n + mycol) : 0u;
   const M ym = __ldg(ymag + tile * kLanes + lane);
@@ -266,7 +290,7 @@ __global__ void __launch_bounds__(256) vn_rows4_kernel(const DevCode c, int cls,
   const int cnt = min(N, count - q0);
   const bool on = lane < cnt * d;
   const int e = on ? __ldg(c.vrow + c.vclass_toff[cls] + int64_t(q0) * d + lane) : 0;  // row << 6 | degree - 1
-  const uint32_t T = warp_transpose32(on ? __ldg(rsgn + int64_t(tile) * c.m_tot + (e >> 6)) : 0u);
+  const uint32_t T = warp_transpose32(on ? __ldg(rsgn + int64_t(e >> 6) * gridDim.y + tile) : 0u);
   const int rel = on ? (e & 63) + 1 - c.min_row_deg : 0;  // 0 .. 2^NB - 1
   const uint32_t b0 = __ballot_sync(kFull, rel & 1), b1 = NB > 1 ? __ballot_sync(kFull, (rel >> 1) & 1) : 0u;
   const int mycol = lane < cnt ? __ldg(c.vnode + first + q0 + lane) : 0;
@@ -421,8 +445,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const in
 // blockIdx.y): every edge's words for those tiles are one coalesced line. The
 // failing lanes of each tile are ORed over the warp's rows and then into
 // fail[tile][l], once per matrix met.
-constexpr int kSynRows = 8;
-
 template <int DMAX>
 __global__ void __launch_bounds__(256) syn_kernel(const DevCode c, int n_tiles, const uint32_t* __restrict__ xh,
                                                   const uint32_t* __restrict__ ztt,
@@ -501,8 +523,9 @@ void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l
   const dim3 grid(blocks_for(q.p1 - q.p0, 8), st.n_tiles);
   if constexpr (!FIXED && DMAX <= 32) {
     if (q.rows == 1) {  // iteration 1 in row form: the rows' sign words and the magnitude table
-      first_rows_kernel<DMAX><<<dim3(blocks_for(c.m_tot, 256), st.n_tiles), 256, 0, s>>>(c, q.yt, st.zt, st.active,
-                                                                                        st.rsgn, st.counters);
+      first_rows_kernel<DMAX><<<dim3(blocks_for(c.m_tot, 8 * kSynRows), unsigned((st.n_tiles + kLanes - 1) / kLanes)),
+                                256, 0, s>>>(c, st.n_tiles, st.xh, st.ztt, q.yt, st.ppos, st.active, st.rsgn,
+                                             st.counters);
       const int cells = st.n_tiles * c.max_row_deg * kLanes;
       first_mag_kernel<M, S><<<blocks_for(cells, 256), 256, 0, s>>>(st.n_tiles, c.max_row_deg,
                                                                    static_cast<const M*>(st.chan_mag), M(l_max),
