@@ -256,15 +256,18 @@ int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int fram
  * entry point decodes frames of several codes in one call: G groups; group g holds F_g
  * frames of its own code (n, rate, u and the QBER of each frame may all
  * differ between groups) with the same per-frame semantics as
- * mbp_decode_batch / mbp_decode_bsc. Every iteration runs one persistent
- * check-node kernel per check-degree class (at most 8 classes per batch), one
- * variable-node kernel and one syndrome kernel per class over the frames of
- * all groups that are still decoding, or (grid kernels, the default unless
- * mbp_autotune_multi finds the persistent ones faster) every group's
- * streaming-schedule kernels; a single-block kernel retires finished frames
- * and rebuilds the work lists on the device. The loop is one CUDA graph
- * with a WHILE node (built on first use for each workspace, batch shape and
- * launch shape, then cached by the library), so the call is asynchronous on
+ * mbp_decode_batch / mbp_decode_bsc. Every iteration runs either every
+ * group's streaming-schedule kernels (grid kernels, the default unless
+ * mbp_autotune_multi finds the other form faster; each group in a conditional
+ * branch of its own, skipped once its frames have all finished), or one
+ * persistent check-node kernel per check-degree class (at most 8 classes per
+ * batch), one variable-node kernel and one syndrome kernel per class over the
+ * frames of all groups that are still decoding; a single-block kernel retires
+ * finished frames and sets the graph's conditions (and, for the persistent
+ * kernels, rebuilds their work lists on the device). The loop is one CUDA
+ * graph with a WHILE node (built on first use for each workspace, batch
+ * shape, launch shape and group state, then cached by the library; destroying
+ * a code drops the graphs that name it), so the call is asynchronous on
  * `stream`: it returns once the work is queued. opts->validate = 1 adds one host
  * synchronisation per group (the non-finite check), and while kernel
  * accounting (mbp_profile_enable) is on the loop is driven from the host with
