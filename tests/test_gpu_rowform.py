@@ -96,3 +96,29 @@ def test_row_form_export_after_one_and_two_iterations(mbp):
         for f in (0, 17, 39):
             c = mbp.mbp_export_c2v(codes, F, out["workspace"], f).cpu().numpy()
             assert np.max(np.abs(c - ref[f])) <= 1e-3, (t, f)
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_more_than_32_tiles(mbp, msg):
+    """1115 frames = 35 tiles: the kernels that take one tile per lane (stopping test, iteration-1 row signs)
+    run a second, ragged chunk of 3 tiles. Streaming (row form) equals the persistent per-edge kernels, and a
+    sample of frames from both chunks equals the oracle's bits where it converges."""
+    H, qber = code("narrow", n=2000)
+    n, F = H[0].n, 35 * 32 - 5
+    x, y, e = mi.bsc_frames(n, F, 0.04, seed=92)
+    codes = mbp.mbp_create_codes(H)
+    z = mbp.mbp_syndrome(codes, dev(i32(x)))
+    dt = {"f32": mbp.MSG_F32, "f16": mbp.MSG_F16}[msg]
+    yd, ed = dev(i32(y)), dev(e)
+    a = mbp.mbp_decode_bsc(codes, yd, ed, z, 30, msg_dtype=dt, want_soft=True, schedule=mbp.SCHED_STREAMING)
+    g = [dict(codes=codes, z_bits=z, F=F, y_bits=yd, qber=ed)]
+    mbp.mbp_multi_set_tuning(g, dict(grid_kernels=0, cn_warps=8, cn_waves=1, vn_warps=8, syn_warps=8), msg_dtype=dt)
+    b = mbp.mbp_decode_multi(g, 30, msg_dtype=dt, want_soft=True)[0]
+    torch.cuda.synchronize()
+    for k in KEYS:
+        assert torch.equal(a[k], b[k]), (msg, k)
+    idx = np.r_[0:24, 1020:1060, F - 24:F]
+    ref = orc.decode(H, orc.bsc_llr(y[idx], n, e[idx]), orc.syndrome(H, x[idx]), 30, threads=8)
+    conv = ref["success"].astype(bool) & a["success"].cpu().numpy()[idx].astype(bool)
+    assert conv.sum() >= 70
+    assert np.array_equal(a["x_hat_bits"].cpu().numpy().view(np.uint32)[idx][conv], ref["x_hat_bits"][conv])
