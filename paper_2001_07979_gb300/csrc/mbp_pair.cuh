@@ -485,6 +485,8 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
   }
   const float ym0 = h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
   const float ym1 = h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
+  const uint32_t a0b = __float_as_uint(ma[0]), da = __float_as_uint(ma[1 % (1 << NB)]) - a0b;
+  const uint32_t b0b = __float_as_uint(mb[0]), db = __float_as_uint(mb[1 % (1 << NB)]) - b0b;
   for (int j = 0; j < cnt; ++j) {
     const int v = __shfl_sync(kFull, mycol, j);
     const uint32_t yl0 = (__shfl_sync(kFull, my0, j) >> lane) & 1u, yl1 = (__shfl_sync(kFull, my1, j) >> lane) & 1u;
@@ -495,18 +497,17 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
 #pragma unroll
     for (int k = 0; k < D; ++k)
       if (k < d) {
-        const bool c0 = r0 & (1u << k);
-        float x0, x1;
-        if constexpr (NB == 1) {
-          x0 = c0 ? ma[1] : ma[0];
-          x1 = c0 ? mb[1] : mb[0];
+        if constexpr (NB == 1) {  // bit patterns by integer multiply-adds, as in vn_rows4_kernel
+          const uint32_t rb = (r0 >> k) & 1u;
+          sum0 += __uint_as_float(a0b + rb * da + ((sg0 >> k) & 1u) * 0x80000000u);
+          sum1 += __uint_as_float(b0b + rb * db + ((sg1 >> k) & 1u) * 0x80000000u);
         } else {
-          const bool c1 = r1 & (1u << k);
-          x0 = c1 ? (c0 ? ma[3] : ma[2]) : (c0 ? ma[1] : ma[0]);
-          x1 = c1 ? (c0 ? mb[3] : mb[2]) : (c0 ? mb[1] : mb[0]);
+          const bool c0 = r0 & (1u << k), c1 = r1 & (1u << k);
+          const float x0 = c1 ? (c0 ? ma[3] : ma[2]) : (c0 ? ma[1] : ma[0]);
+          const float x1 = c1 ? (c0 ? mb[3] : mb[2]) : (c0 ? mb[1] : mb[0]);
+          sum0 += Bits<float>::copy_sign(x0, sg0 << (31 - k));
+          sum1 += Bits<float>::copy_sign(x1, sg1 << (31 - k));
         }
-        sum0 += Bits<float>::copy_sign(x0, sg0 << (31 - k));
-        sum1 += Bits<float>::copy_sign(x1, sg1 << (31 - k));
       }
     if (h0) {
       if (t.s0) lv[(n0 + v) * kLanes + lane] = sum0;

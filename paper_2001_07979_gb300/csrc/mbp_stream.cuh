@@ -302,6 +302,11 @@ __global__ void __launch_bounds__(256) vn_rows4_kernel(const DevCode c, int cls,
 #pragma unroll
   for (int i = 0; i < (1 << NB); ++i) mg[i] = __ldg(fm + min(g0 + i, kMaxRowDeg - 1) * kLanes);
   const M ym = __ldg(ymag + tile * kLanes + lane);
+  [[maybe_unused]] uint32_t m0b = 0, dmb = 0;
+  if constexpr (NB == 1 && sizeof(M) == 4) {
+    m0b = __float_as_uint(float(mg[0]));
+    dmb = __float_as_uint(float(mg[1])) - m0b;
+  }
   for (int j = 0; j < cnt; ++j) {
     const int col = __shfl_sync(kFull, mycol, j);
     const uint32_t yl = (__shfl_sync(kFull, myy, j) >> lane) & 1u;
@@ -312,10 +317,17 @@ __global__ void __launch_bounds__(256) vn_rows4_kernel(const DevCode c, int cls,
 #pragma unroll
     for (int k = 0; k < D; ++k)
       if (k < d) {
-        M m;
-        if constexpr (NB == 1) m = (r0 & (1u << k)) ? mg[1] : mg[0];
-        else m = (r1 & (1u << k)) ? ((r0 & (1u << k)) ? mg[3] : mg[2]) : ((r0 & (1u << k)) ? mg[1] : mg[0]);
-        sum += Bits<M>::copy_sign(m, sg << (31 - k));
+        if constexpr (NB == 1 && sizeof(M) == 4) {
+          // the signed magnitude's bit pattern by integer multiply-adds (the FMA pipe): the degree bit picks
+          // m1 over m0, the sign bit sets bit 31 (both magnitudes are non-negative)
+          const uint32_t rb = (r0 >> k) & 1u, sb = (sg >> k) & 1u;
+          sum += __uint_as_float(m0b + rb * dmb + sb * 0x80000000u);
+        } else {
+          M m;
+          if constexpr (NB == 1) m = (r0 & (1u << k)) ? mg[1] : mg[0];
+          else m = (r1 & (1u << k)) ? ((r0 & (1u << k)) ? mg[3] : mg[2]) : ((r0 & (1u << k)) ? mg[1] : mg[0]);
+          sum += Bits<M>::copy_sign(m, sg << (31 - k));
+        }
       }
     if ((act >> lane) & 1u) lv[(node0 + col) * kLanes + lane] = sum;
     const uint32_t hard = __ballot_sync(kFull, sum < M(0));
