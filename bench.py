@@ -388,7 +388,8 @@ def run_gb300(args):
         traffic = kernel_traffic(iters, n_dom // args.steps if n_dom else 0, "resident_kernel_n65536.txt", args.msg_dtype)
     else:
         n_dom, ms_dom = prof["check"]
-        kernel_name = "cn_kernel (check-node update, eq. 6, per-edge messages)"
+        kernel_name = ("check-node update of eq. 6 on per-edge messages (cn_pair_kernel: one warp per tile pair "
+                       "and row for rows of up to 24 edges, else cn_kernel)")
         rule = ("per frame: 2*s*E+4n per iteration after the second (iterations 1 and 2 run in row form)" if rows
                 else "per frame: s*E+4n per iteration, plus s*E per iteration after the first")
         b_dom = b_check

@@ -151,17 +151,23 @@ struct Store<__nv_bfloat16> {
 };
 
 // Message addressing (the layout of mbp_internal.h): slot k of a tile's row is
-// kMsgStride<S> elements after slot k - 1; 2-byte messages interleave the tiles
-// of a pair, lane by lane.
+// kMsgStride<S> elements after slot k - 1. Tiles 2q and 2q + 1 share each
+// slot: 2-byte messages interleave them lane by lane (one 128-byte line), 4-byte
+// messages put them in two adjacent 128-byte lines, so a kernel of one tile
+// still reads whole lines and a kernel of the pair gathers 256 contiguous bytes
+// per edge (random 256-byte units run at the copy bandwidth on GB300, random
+// 128-byte lines at about two thirds of it).
 template <typename S>
-constexpr int kMsgTiles = sizeof(S) == 2 ? 2 : 1;
+constexpr int kMsgTiles = sizeof(S) <= 4 ? 2 : 1;
 template <typename S>
 constexpr int kMsgStride = kLanes * kMsgTiles<S>;
 // Element of (tile, slot 0, lane).
 template <typename S>
 __device__ __forceinline__ int64_t msg_at(int tile, int s_tot, int lane) {
   constexpr int P = kMsgTiles<S>;
-  return int64_t(tile / P) * s_tot * kMsgStride<S> + lane * P + tile % P;
+  const int64_t q = int64_t(tile / P) * s_tot * kMsgStride<S>;
+  if constexpr (sizeof(S) == 2) return q + lane * P + tile % P;
+  else return q + (tile % P) * kLanes + lane;
 }
 
 // Memory policies.
@@ -562,8 +568,10 @@ __device__ __forceinline__ void cn_tile_row(const DevCode& c, int tile, int p, u
 
 // Sum of one node's messages, D >= its degree: the slot indices are loaded
 // first, then all gathers are in flight together; the sum runs in stacked-row
-// order (the order of col_slot).
-template <typename M, typename S, int D, int POL>
+// order (the order of col_slot). STRIDE: elements from one slot to the next
+// (the decoder's message layout by default; buffers of one tile per slot pass
+// kLanes).
+template <typename M, typename S, int D, int POL, int STRIDE = kMsgStride<S>>
 __device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const S* __restrict__ msg, M sum) {
   int slot[D];
 #pragma unroll
@@ -571,7 +579,7 @@ __device__ __forceinline__ M vn_sum(const int* __restrict__ slots, int d, const 
   M g[D];
 #pragma unroll
   for (int k = 0; k < D; ++k)
-    g[k] = slot[k] >= 0 ? M(Store<S>::widen(ld_msg<POL>(msg + int64_t(slot[k]) * kMsgStride<S>))) : M(0);
+    g[k] = slot[k] >= 0 ? M(Store<S>::widen(ld_msg<POL>(msg + int64_t(slot[k]) * STRIDE))) : M(0);
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (slot[k] >= 0) sum += g[k];

@@ -38,8 +38,10 @@ constexpr int kMaxVClasses = 8;  // variable-node degree classes with slot table
 constexpr int kMaxQBits = 24;   // fixed-point accumulation: at most 2^-24 resolution
 constexpr int kMinQBits = 12;   // and at least 2^-12
 
-// Tiles that share one message line: 2 for 2-byte messages, else 1.
-constexpr int msg_pair(size_t msg_bytes) { return msg_bytes == 2 ? 2 : 1; }
+// Tiles whose messages of one edge are stored together: 2 for 2- and 4-byte
+// messages (2-byte: one 128-byte line, the tiles interleaved lane by lane;
+// 4-byte: two adjacent 128-byte lines, one per tile), else 1.
+constexpr int msg_pair(size_t msg_bytes) { return msg_bytes <= 4 ? 2 : 1; }
 // Tiles of message storage for n_tiles tiles (rounded up to whole pairs).
 constexpr size_t msg_tiles(size_t n_tiles, size_t msg_bytes) {
   return (n_tiles + msg_pair(msg_bytes) - 1) / msg_pair(msg_bytes) * msg_pair(msg_bytes);

@@ -157,10 +157,10 @@ __global__ void __launch_bounds__(256) nbp_vn_fwd_kernel(const DevCode c, const 
   const int d = c.col_ptr[col + 1] - a0;
   const int* slots = c.col_slot + a0;
   float sum = lp[at];
-  if (d <= 4) sum = vn_sum<float, float, 4, kPolStream>(slots, d, msg, sum);
-  else if (d <= 8) sum = vn_sum<float, float, 8, kPolStream>(slots, d, msg, sum);
+  if (d <= 4) sum = vn_sum<float, float, 4, kPolStream, kLanes>(slots, d, msg, sum);
+  else if (d <= 8) sum = vn_sum<float, float, 8, kPolStream, kLanes>(slots, d, msg, sum);
   else
-    for (int q = 0; q < d; q += 16) sum = vn_sum<float, float, 16, kPolStream>(slots + q, d - q, msg, sum);
+    for (int q = 0; q < d; q += 16) sum = vn_sum<float, float, 16, kPolStream, kLanes>(slots + q, d - q, msg, sum);
   lout[at] = sum;
 }
 
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) nbp_vn_bwd_kernel(const DevCode c, const 
     const int a0 = c.col_ptr[col];
     const int d = c.col_ptr[col + 1] - a0;
     const int* slots = c.col_slot + a0;
-    for (int q = 0; q < d; q += 16) sum = vn_sum<float, float, 16, kPolStream>(slots + q, d - q, msg, sum);
+    for (int q = 0; q < d; q += 16) sum = vn_sum<float, float, 16, kPolStream, kLanes>(slots + q, d - q, msg, sum);
   }
   if (lbar) lbar[at] = sum;
   if (lpbar) lpbar[at] = lpbar_init ? sum : lpbar[at] + sum;

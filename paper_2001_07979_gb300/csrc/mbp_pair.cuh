@@ -1,15 +1,17 @@
-// Streaming kernels of 2-byte message storage (FP16 / BF16 messages, FP32
-// arithmetic). The messages of tiles 2q and 2q + 1 share one 128-byte line per
-// edge (msg_at): one warp takes the pair, each lane the same frame position of
-// both tiles, so every message access is one 32-bit word per lane (a full
-// line per warp) and the row's columns and slots are loaded once for 64 frames.
-// Per frame the arithmetic is that of cn_row / cn_row_signs / vn_class_nodes,
-// in the same order, so a frame's messages and posteriors do not depend on the
-// kernel that produced them.
+// Streaming kernels of tile pairs (FP32, FP16 and BF16 messages; FP32
+// arithmetic). Tiles 2q and 2q + 1 store the messages of an edge together
+// (msg_at): 2-byte messages in one 128-byte line, one 32-bit word per lane;
+// 4-byte messages in two adjacent 128-byte lines. One warp takes the pair, each
+// lane the same frame position of both tiles, so every message access of the
+// warp covers the pair's whole unit (128 or 256 contiguous bytes) and the row's
+// columns and slots are loaded once for 64 frames. Per frame the arithmetic is
+// that of cn_row / cn_row_signs / vn_class_nodes, in the same order, so a
+// frame's messages and posteriors do not depend on the kernel that produced
+// them.
 //
 // A tile whose frames have all retired (or the missing partner of an odd tile
 // count) is neither read nor written; in a pair with one live tile, a lane
-// writes only the halves of its live frames.
+// writes only its live frames' messages.
 #pragma once
 
 #include <type_traits>
@@ -19,43 +21,66 @@
 namespace mbp {
 namespace dev {
 
+// Per storage type: T, the element type a lane addresses (one per slot and lane
+// for 2-byte pairs); kSlot, the T elements from one slot of a pair to the next;
+// W, what a lane loads for both tiles' message of an edge.
 template <typename S>
 struct Pair;
 
 template <>
 struct Pair<__half> {
   using T = __half2;
+  using W = uint32_t;  // low half: tile 2q
+  static constexpr int kSlot = kLanes;
   static __device__ __forceinline__ T narrow(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
 template <>
 struct Pair<__nv_bfloat16> {
   using T = __nv_bfloat162;
+  using W = uint32_t;
+  static constexpr int kSlot = kLanes;
   static __device__ __forceinline__ T narrow(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
 
-// The word of both tiles' message of an edge (low half: tile 2q).
+template <>
+struct Pair<float> {
+  using T = float;  // tile 2q at the lane's element, tile 2q + 1 one line (kLanes elements) later
+  using W = float2;
+  static constexpr int kSlot = 2 * kLanes;
+};
+
+// Both tiles' message of an edge.
 template <typename S>
-__device__ __forceinline__ uint32_t ld_pair(const typename Pair<S>::T* p) {
-  return __ldcs(reinterpret_cast<const unsigned int*>(p));
+__device__ __forceinline__ typename Pair<S>::W ld_pair(const typename Pair<S>::T* p) {
+  if constexpr (std::is_same<S, float>::value) return make_float2(__ldcs(p), __ldcs(p + kLanes));
+  else return __ldcs(reinterpret_cast<const unsigned int*>(p));
 }
 
-// s0 += lo(w), s1 += hi(w), and v0 -= lo(w), v1 -= hi(w): sm_100's mixed-precision
-// add / fma take the 16-bit operand as is (its widening to FP32 is exact), so each
-// is the FP32 operation on the widened message with one rounding, in one instruction.
+// s0 += message of tile 2q, s1 += message of tile 2q + 1, and v0 -= ..., v1 -= ...
+// as FP32 operations with one rounding each. For 2-byte messages sm_100's
+// mixed-precision add / fma take the 16-bit operand as is (its widening to FP32
+// is exact), in one instruction.
 template <typename S>
-__device__ __forceinline__ void add_pair(float& s0, float& s1, uint32_t w) {
-  if constexpr (std::is_same<S, __half>::value)
+__device__ __forceinline__ void add_pair(float& s0, float& s1, typename Pair<S>::W w) {
+  if constexpr (std::is_same<S, float>::value) {
+    s0 += w.x;
+    s1 += w.y;
+  } else if constexpr (std::is_same<S, __half>::value) {
     asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; add.rn.f32.f16 %0, l, %0; add.rn.f32.f16 %1, h, %1;}"
         : "+f"(s0), "+f"(s1) : "r"(w));
-  else
+  } else {
     asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; add.rn.f32.bf16 %0, l, %0; add.rn.f32.bf16 %1, h, %1;}"
         : "+f"(s0), "+f"(s1) : "r"(w));
+  }
 }
 
 template <typename S>
-__device__ __forceinline__ void sub_pair(float& v0, float& v1, uint32_t w) {
-  if constexpr (std::is_same<S, __half>::value) {
+__device__ __forceinline__ void sub_pair(float& v0, float& v1, typename Pair<S>::W w) {
+  if constexpr (std::is_same<S, float>::value) {
+    v0 -= w.x;
+    v1 -= w.y;
+  } else if constexpr (std::is_same<S, __half>::value) {
     const unsigned short m1 = 0xBC00u;  // -1 in FP16
     asm("{.reg .b16 l, h; mov.b32 {l, h}, %2; fma.rn.f32.f16 %0, l, %3, %0; fma.rn.f32.f16 %1, h, %3, %1;}"
         : "+f"(v0), "+f"(v1) : "r"(w), "h"(m1));
@@ -66,10 +91,13 @@ __device__ __forceinline__ void sub_pair(float& v0, float& v1, uint32_t w) {
   }
 }
 
-// Store a lane's two messages; a retired frame keeps its stored half.
+// Store a lane's two messages; a retired frame keeps its stored message.
 template <typename S>
 __device__ __forceinline__ void st_pair(typename Pair<S>::T* p, float a, float b, bool s0, bool s1) {
-  if (s0 && s1) {
+  if constexpr (std::is_same<S, float>::value) {
+    if (s0) __stcs(p, a);
+    if (s1) __stcs(p + kLanes, b);
+  } else if (s0 && s1) {
     __stcs(p, Pair<S>::narrow(a, b));
   } else {
     S* h = reinterpret_cast<S*>(p);
@@ -166,7 +194,7 @@ __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ col
   } else if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      if (!CHECKED || k < deg) sub_pair<S>(v0[k], v1[k], ld_pair<S>(msg + k * kLanes));
+      if (!CHECKED || k < deg) sub_pair<S>(v0[k], v1[k], ld_pair<S>(msg + k * Pair<S>::kSlot));
   }
   if (!s0 && !s1) return;
   // tile 0, then tile 1, sharing the prefix array; tile 0's outputs replace its deltas in v0
@@ -186,7 +214,7 @@ __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ col
   for (int k = D - 1; k >= 0; --k) {
     if (!CHECKED || k < deg) {
       const float m1 = A::clipped_mag(A::oplus(pre[k], q), l_max);
-      st_pair<S>(msg + k * kLanes, v0[k], B::copy_sign(m1, par1 ^ B::sign_word(v1[k])), s0, s1);
+      st_pair<S>(msg + k * Pair<S>::kSlot, v0[k], B::copy_sign(m1, par1 ^ B::sign_word(v1[k])), s0, s1);
     }
     q = A::oplus(q, fabsf(v1[k]));
   }
@@ -219,7 +247,7 @@ __device__ __forceinline__ void cn_pair_row_signs(int deg, const int* __restrict
 #pragma unroll
   for (int k = 0; k < D; ++k)
     if (!CHECKED || k < deg)
-      st_pair<S>(msg + k * kLanes, Bits<float>::copy_sign(m0, par0 ^ (((b0 >> k) & 1u) << 31)),
+      st_pair<S>(msg + k * Pair<S>::kSlot, Bits<float>::copy_sign(m0, par0 ^ (((b0 >> k) & 1u) << 31)),
                  Bits<float>::copy_sign(m1, par1 ^ (((b1 >> k) & 1u) << 31)), s0, s1);
 }
 
@@ -249,7 +277,7 @@ __global__ void __launch_bounds__(256, cn_pair_min_blocks(DMAX))
   const uint32_t par0 = h0 ? ((zt[int64_t(t.t0) * c.m_tot + p] >> lane) & 1u) << 31 : 0u;
   const uint32_t par1 = h1 ? ((zt[int64_t(t.t1) * c.m_tot + p] >> lane) & 1u) << 31 : 0u;
   using T = typename Pair<S>::T;
-  T* msg = reinterpret_cast<T*>(c2v) + (int64_t(blockIdx.y) * c.s_tot + base) * kLanes + lane;
+  T* msg = reinterpret_cast<T*>(c2v) + (int64_t(blockIdx.y) * c.s_tot + base) * Pair<S>::kSlot + lane;
   const float* g0 = lsrc + int64_t(t.t0) * c.n * kLanes + lane;
   const float* g1 = h1 ? lsrc + int64_t(t.t1) * c.n * kLanes + lane : g0;
   const int* cols = c.slot_col + base;
@@ -295,7 +323,7 @@ __global__ void __launch_bounds__(256) cn_first_pair_kernel(const DevCode c, int
   const float ym0 = h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
   const float ym1 = h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
   using T = typename Pair<S>::T;
-  T* msg = reinterpret_cast<T*>(c2v) + (int64_t(blockIdx.y) * c.s_tot + base) * kLanes + lane;
+  T* msg = reinterpret_cast<T*>(c2v) + (int64_t(blockIdx.y) * c.s_tot + base) * Pair<S>::kSlot + lane;
   const uint32_t* y0 = yt + int64_t(t.t0) * c.n;
   const uint32_t* y1 = h1 ? yt + int64_t(t.t1) * c.n : y0;
   const int* cols = c.slot_col + base;
@@ -307,8 +335,9 @@ __global__ void __launch_bounds__(256) cn_first_pair_kernel(const DevCode c, int
 }
 
 // Eq. (2) and the hard decision for N nodes of one degree class (degree d <= D)
-// of both tiles: every gather is one 32-bit word per lane (both tiles' C2V of
-// the edge), the sums run in stacked-row order as in vn_class_nodes.
+// of both tiles: every gather covers both tiles' C2V of the edge (one 32-bit
+// word per lane, or two adjacent lines for FP32), the sums run in stacked-row
+// order as in vn_class_nodes.
 template <typename S, int D, int N>
 __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int cls, const S* __restrict__ c2v,
                                                             float* __restrict__ lv, const float* __restrict__ lp,
@@ -326,20 +355,20 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
   const int cnt = min(N, count - qq);
   const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
   using T = typename Pair<S>::T;
-  const T* msg = reinterpret_cast<const T*>(c2v) + int64_t(blockIdx.y) * c.s_tot * kLanes + lane;
+  const T* msg = reinterpret_cast<const T*>(c2v) + int64_t(blockIdx.y) * c.s_tot * Pair<S>::kSlot + lane;
   const int32_t* slots0 = c.vslot + c.vclass_toff[cls] + int64_t(qq) * d;
   int col[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) col[j] = j < cnt ? __ldg(c.vnode + first + qq + j) : 0;
   const int64_t n0 = int64_t(t.t0) * c.n, n1 = int64_t(t.t1) * c.n;
-  uint32_t g[N][D];
+  typename Pair<S>::W g[N][D];
 #pragma unroll
   for (int j = 0; j < N; ++j)
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const bool on = j < cnt && k < d;
       const int slot = on ? __ldg(slots0 + j * d + k) : 0;
-      g[j][k] = on ? ld_pair<S>(msg + int64_t(slot) * kLanes) : 0u;
+      g[j][k] = on ? ld_pair<S>(msg + int64_t(slot) * Pair<S>::kSlot) : typename Pair<S>::W{};
     }
   const float ym0 = yt && h0 ? __ldg(ymag + t.t0 * kLanes + lane) : 0.f;
   const float ym1 = yt && h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
@@ -377,9 +406,8 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
   }
 }
 
-// vn_rows_kernel for a tile pair (FP16 / BF16 messages, whose row-form magnitudes
-// are stored rounded to the message type): each lane sums its frame in both
-// tiles.
+// vn_rows_kernel for a tile pair (the row-form magnitudes of 2-byte messages are
+// stored rounded to the message type): each lane sums its frame in both tiles.
 template <int D>
 __global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int cls, float* __restrict__ lv,
                                                            const uint32_t* __restrict__ yt,

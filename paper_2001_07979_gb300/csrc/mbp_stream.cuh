@@ -32,6 +32,12 @@ inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) /
 // test, first-iteration row signs).
 constexpr int kSynRows = 8;
 
+// FP32 arithmetic on 2- or 4-byte messages stored in tile pairs (msg_at): the
+// check and variable-node passes of the sum-product rule take a tile pair per
+// warp (mbp_pair.cuh).
+template <typename M, typename S>
+constexpr bool kPairKernels = sizeof(M) == 4 && sizeof(S) <= 4;
+
 // Resident blocks of 256 threads the check kernel is compiled for: 5 per SM (48
 // registers, no spills) for float rows of up to 14 edges, more latency hiding
 // than the 4 that 64 registers allow; longer rows (and FP64) keep the
@@ -41,32 +47,43 @@ constexpr int cn_min_blocks(int dmax) {
   return sizeof(M) == 4 && dmax <= 14 ? 5 : 1;
 }
 
-// One warp per (tile, check row): 8 rows per block, tile = blockIdx.y, rows
-// p0 .. p1 - 1 (every row for flooding, one matrix's rows for the serial order).
+// One warp per (tile, check row): 8 rows per block, rows p0 .. p1 - 1 (every
+// row for flooding, one matrix's rows for the serial order). Tiles that share
+// message slots (msg_at) run side by side: the blocks of tiles 2q and 2q + 1
+// alternate along x (cn_grid), so both lines of an edge's slot are read and
+// written at about the same time; otherwise tile = blockIdx.y.
 // RIN: iteration 2 after a row-form iteration 1 (the old messages are rebuilt
 // from fmag / rsgn and Bob's sign words yt); the kernel then clears the row-form
 // flag counters[2], as the messages are per edge again.
+template <typename S>
+inline dim3 cn_grid(int rows, int n_tiles) {
+  if (kMsgTiles<S> == 2) return dim3(2 * blocks_for(rows, 8), unsigned((n_tiles + 1) / 2));
+  return dim3(blocks_for(rows, 8), unsigned(n_tiles));
+}
+
 template <typename M, typename S, int DMAX, bool FIXED, bool RIN = false>
 __global__ void __launch_bounds__(256, cn_min_blocks<M>(DMAX)) cn_kernel(const DevCode c, int p0, int p1, int first_iter,
                                                  S* __restrict__ c2v, const M* __restrict__ lsrc,
                                                  const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
                                                  const uint32_t* __restrict__ zt,
-                                                 const uint32_t* __restrict__ active, M l_max,
+                                                 const uint32_t* __restrict__ active, int n_tiles, M l_max,
                                                  int32_t* __restrict__ lacc, float qscale,
                                                  const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn,
                                                  int32_t* __restrict__ counters) {
   if (RIN && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[2] = 0;
-  const int tile = blockIdx.y;
+  constexpr bool kPaired = kMsgTiles<S> == 2;
+  const int tile = kPaired ? 2 * int(blockIdx.y) + int(blockIdx.x & 1u) : int(blockIdx.y);
+  if (tile >= n_tiles) return;
   const uint32_t act = active[tile];
   if (act == 0) return;
-  const int p = p0 + blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int p = p0 + int(kPaired ? blockIdx.x >> 1 : blockIdx.x) * 8 + (threadIdx.x >> 5);
   if (p >= p1) return;
   CnView<M, S> v = cn_view<M, S, kPolStream>(c, tile, act, first_iter, c2v, lsrc, yt, ymag, zt,
                                              FIXED ? lacc : nullptr);
   if constexpr (RIN) {
     v.rm = fmag + int64_t(tile) * kMaxRowDeg * kLanes + (threadIdx.x & 31);
     v.rs = rsgn + tile;
-    v.rs_nt = gridDim.y;
+    v.rs_nt = n_tiles;
     v.yprev = yt + int64_t(tile) * c.n;
   }
   cn_view_row<M, S, DMAX, FIXED, kPolStream, RIN>(v, p, first_iter, l_max, Arith<M>::delta(l_max), qscale);
@@ -356,7 +373,7 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
       if (rows) {  // classes of up to 16 edges (rows_ok), 32 / d nodes per warp
         const int per_warp = kLanes / d;
         const unsigned blocks = blocks_for(count, 8 * per_warp);
-        if constexpr (sizeof(S) == 2) {
+        if constexpr (kPairKernels<M, S>) {
           const unsigned pairs = unsigned((st.n_tiles + 1) / 2);
 #define MBP_VR2(K, ...)                                                                                        \
   K<__VA_ARGS__><<<dim3(blocks, pairs), 256, 0, s>>>(c, k, static_cast<float*>(st.lv), st.yt,                    \
@@ -398,7 +415,7 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
         }
         continue;
       }
-      if constexpr (sizeof(S) == 2) {  // tile pairs for classes of up to 16 edges
+      if constexpr (kPairKernels<M, S>) {  // tile pairs for classes of up to 16 edges
         const unsigned pairs = unsigned((st.n_tiles + 1) / 2);
 #define MBP_VN2(D, N)                                                                                         \
   vn_class_pair_kernel<S, D, N><<<dim3(blocks_for(count, 8 * N), pairs), 256, 0, s>>>(                        \
@@ -546,7 +563,11 @@ void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l
     }
   }
   const M* rm_in = q.rows == 2 ? static_cast<const M*>(st.fmag) : nullptr;
-  if constexpr (sizeof(S) == 2 && !FIXED && DMAX <= 24) {  // tile pairs (mbp_pair.cuh)
+  // Tile pairs (mbp_pair.cuh): every sum-product pass of rows up to 24 edges. On the paired FP32 layout the
+  // pair kernel measured faster than the one-tile cn_kernel for rows of 14 edges (iteration 2, issue-bound,
+  // shares the row's loads between two tiles; later iterations, memory-bound, keep a row's two lines per
+  // slot in one warp) and of 21 edges (whole decodes at rate 0.8: 7 to 11% more throughput).
+  if constexpr (kPairKernels<M, S> && !FIXED && DMAX <= 24) {
     if (rule == MBP_RULE_SUM_PRODUCT) {
       const dim3 pgrid(grid.x, unsigned((st.n_tiles + 1) / 2));
       if (q.first_iter && q.yt)
@@ -585,17 +606,17 @@ void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l
   }
   if constexpr (!FIXED && DMAX <= 32) {
     if (rm_in) {
-      cn_kernel<M, S, DMAX, false, true><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
-                                                              static_cast<const M*>(q.lsrc), st.yt,
-                                                              static_cast<const M*>(st.chan_mag), st.zt, st.active,
-                                                              M(l_max), st.lacc, qscale, rm_in, st.rsgn, st.counters);
+      cn_kernel<M, S, DMAX, false, true><<<cn_grid<S>(q.p1 - q.p0, st.n_tiles), 256, 0, s>>>(
+          c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v), static_cast<const M*>(q.lsrc), st.yt,
+          static_cast<const M*>(st.chan_mag), st.zt, st.active, st.n_tiles, M(l_max), st.lacc, qscale, rm_in,
+          st.rsgn, st.counters);
       return;
     }
   }
-  cn_kernel<M, S, DMAX, FIXED><<<grid, 256, 0, s>>>(c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v),
-                                                 static_cast<const M*>(q.lsrc), q.yt,
-                                                 static_cast<const M*>(st.chan_mag), st.zt, st.active, M(l_max),
-                                                 st.lacc, qscale, nullptr, nullptr, st.counters);
+  cn_kernel<M, S, DMAX, FIXED><<<cn_grid<S>(q.p1 - q.p0, st.n_tiles), 256, 0, s>>>(
+      c, q.p0, q.p1, q.first_iter, static_cast<S*>(st.c2v), static_cast<const M*>(q.lsrc), q.yt,
+      static_cast<const M*>(st.chan_mag), st.zt, st.active, st.n_tiles, M(l_max), st.lacc, qscale, nullptr, nullptr,
+      st.counters);
 }
 
 // Unroll bound at or one above the largest check degree (the last two degrees run without per-edge tests).

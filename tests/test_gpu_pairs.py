@@ -1,5 +1,5 @@
-"""FP16 / BF16 message storage, whose messages pair the tiles 2q and 2q + 1 (one 32-bit word per lane holds
-both tiles' message of an edge), through the C ABI.
+"""Message storage in tile pairs (tiles 2q and 2q + 1 store an edge's messages together: one 32-bit word
+per lane for FP16 / BF16, two adjacent 128-byte lines for FP32), through the C ABI.
 
 Each frame's arithmetic is independent of the other frames: the per-frame outputs of a decode (bits,
 iterations, success, posteriors) must not change, bit for bit, with the batch the frame is decoded in. The
@@ -26,6 +26,9 @@ def mbp():
     import paper_2001_07979_gb300 as m
     m.build()
     return m
+
+
+MSG = {"f32": lambda m: m.MSG_F32, "f16": lambda m: m.MSG_F16, "bf16": lambda m: m.MSG_BF16}
 
 
 def dev(a):
@@ -61,9 +64,9 @@ def mixed(mbp):
     return Mixed(mbp)
 
 
-@pytest.mark.parametrize("msg", ["f16", "bf16"])
-def test_half_storage_frames_independent_of_batch(mbp, mixed, msg):
-    dt = mbp.MSG_F16 if msg == "f16" else mbp.MSG_BF16
+@pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
+def test_pair_storage_frames_independent_of_batch(mbp, mixed, msg):
+    dt = MSG[msg](mbp)
     full = mixed.decode(mbp, np.arange(mixed.F), dt)
     its = full["iters"]
     assert its[:32].max() < its[32:].max()  # the first tile retires before its partner
@@ -77,9 +80,9 @@ def test_half_storage_frames_independent_of_batch(mbp, mixed, msg):
         assert np.array_equal(graph[k], full[k]), (msg, k)
 
 
-@pytest.mark.parametrize("msg", ["f16", "bf16"])
-def test_half_storage_converged_frames_match_oracle(mbp, mixed, msg):
-    dt = mbp.MSG_F16 if msg == "f16" else mbp.MSG_BF16
+@pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
+def test_pair_storage_converged_frames_match_oracle(mbp, mixed, msg):
+    dt = MSG[msg](mbp)
     out = mixed.decode(mbp, np.arange(mixed.F), dt)
     LP = orc.bsc_llr(mixed.y, mixed.n, mixed.e)
     ref = orc.decode(mixed.H, LP, orc.syndrome(mixed.H, mixed.x), 40, threads=8)
@@ -88,11 +91,11 @@ def test_half_storage_converged_frames_match_oracle(mbp, mixed, msg):
     assert np.array_equal(out["x_hat_bits"].view(np.uint32)[conv], ref["x_hat_bits"][conv])
 
 
-@pytest.mark.parametrize("msg", ["f16", "bf16"])
-def test_half_storage_llr_inputs_and_serial_order(mbp, mixed, msg):
+@pytest.mark.parametrize("msg", ["f32", "f16", "bf16"])
+def test_pair_storage_llr_inputs_and_serial_order(mbp, mixed, msg):
     """General LLR inputs (the first iteration reads L_P through the pair kernel) and the matrix-serial order
     (row ranges per matrix, messages cleared to 0 first): converged frames equal the oracle's bits."""
-    dt = mbp.MSG_F16 if msg == "f16" else mbp.MSG_BF16
+    dt = MSG[msg](mbp)
     LP = orc.bsc_llr(mixed.y, mixed.n, mixed.e)
     z_orc = orc.syndrome(mixed.H, mixed.x)
     z = mbp.mbp_syndrome(mixed.codes, dev(i32(mixed.x)))
@@ -123,3 +126,22 @@ def test_half_storage_first_iteration_messages_odd_tiles(mbp):
         c = mbp.mbp_export_c2v(codes, F, out["workspace"], f, mbp.MSG_F16).cpu().numpy()
         # |C2V| <= l_max = 20 < 32: FP16 spacing <= 2^-6 there, rounding error <= 2^-7, plus FP32 arithmetic
         assert np.max(np.abs(c - ref[f])) <= 2.0 ** -7 + 1e-3, f
+
+
+def test_f32_pair_messages_odd_tiles(mbp):
+    """FP32 messages of 70 frames (3 tiles, the third without a partner) after one iteration on LLR inputs
+    (the pair kernel's first iteration) and after two (old messages read back from the pair's two lines):
+    every exported C2V within 1e-3 of the oracle's."""
+    n, F = 2000, 70
+    H = mi.make_codes(n, 800, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 64)
+    x, y, e = mi.bsc_frames(n, F, 0.05, seed=65)
+    codes = mbp.mbp_create_codes(H)
+    z = mbp.mbp_syndrome(codes, dev(i32(x)))
+    LP = orc.bsc_llr(y, n, e)
+    for t in (1, 2):
+        out = mbp.mbp_decode_batch(codes, dev(LP.astype(np.float32)), z, t, early_exit=False,
+                                   schedule=mbp.SCHED_STREAMING)
+        ref = orc.decode(H, LP, orc.syndrome(H, x), t, early_exit=False, want_c2v=True)["c2v"]
+        for f in (0, 31, 32, 63, 64, 69):
+            c = mbp.mbp_export_c2v(codes, F, out["workspace"], f).cpu().numpy()
+            assert np.max(np.abs(c - ref[f])) <= 1e-3, (t, f)
