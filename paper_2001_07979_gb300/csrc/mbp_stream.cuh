@@ -421,7 +421,11 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
   vn_class_pair_kernel<S, D, N><<<dim3(blocks_for(count, 8 * N), pairs), 256, 0, s>>>(                        \
       c, k, static_cast<const S*>(st.c2v), static_cast<float*>(st.lv), static_cast<const float*>(st.lp), st.yt, \
       static_cast<const float*>(st.chan_mag), st.xh, st.active, st.n_tiles)
-        if (d <= 4) { MBP_VN2(4, 4); continue; }
+        // N nodes per warp: small enough for 5 blocks per SM (47-48 registers); the short classes are bound by
+        // each warp's chain of index loads and gathers, so resident warps count for more than gathers per warp
+        // (degree 4: N = 3 over N = 4 and 6; degree 6: an exact D = 6 with N = 2 over D = 8 and over N = 3)
+        if (d <= 4) { MBP_VN2(4, 3); continue; }
+        if (d <= 6) { MBP_VN2(6, 2); continue; }
         if (d <= 8) { MBP_VN2(8, 2); continue; }
         if (d <= 16) { MBP_VN2(16, 1); continue; }
 #undef MBP_VN2
