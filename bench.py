@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -195,12 +196,21 @@ KERNEL_SOURCES = ("mbp_internal.h", "mbp_device.cuh", "mbp_stream.cuh", "mbp_pai
                   "mbp_resident.cuh")
 
 
+def source_code_only(text):
+    """C++ source without its comments and blank lines, each remaining line stripped of trailing blanks (the
+    sources have no comment markers inside string or character literals)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).rstrip() for line in text.splitlines())
+    return "\n".join(line for line in lines if line.strip())
+
+
 def kernel_source_digest():
-    """First 16 hex digits of the SHA-256 of the sources that define the decoder kernels (the key a committed
-    ncu summary records, so that its DRAM figures are used only for the kernels they were measured on)."""
+    """First 16 hex digits of the SHA-256 of the code (comments left out) of the sources that define the decoder
+    kernels: the key a committed ncu summary records, so that its DRAM figures are used only for the kernels
+    they were measured on."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2001_07979_gb300", "csrc", f), "rb").read())
+        h.update(source_code_only(open(os.path.join(ROOT, "paper_2001_07979_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

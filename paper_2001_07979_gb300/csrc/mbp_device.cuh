@@ -5,8 +5,9 @@
 // form a tile; every per-edge or per-node array stores the tile's 32 frames of
 // one edge or node contiguously, so each random access moves one 128-byte line
 // (FP32) and one warp (lane = frame) handles one check row or one variable
-// node of one tile. 2-byte messages interleave two tiles per line (msg_at), and
-// their fast kernels (mbp_pair.cuh) give each lane the frame of both tiles.
+// node of one tile. Message slots are shared by tile pairs (msg_at: FP32 in two
+// adjacent lines, 2-byte messages interleaved in one line), and the fast
+// kernels (mbp_pair.cuh) give each lane the frame of both tiles.
 //
 // Check-node arithmetic. For a check with incoming V2C values v_k, eq. (6) gives
 //   |C2V_k| = 2 atanh( prod_{r != k} tanh(|v_r| / 2) ),

@@ -8,12 +8,13 @@
 //     position p owns the edge "slots" slice_base[p] .. slice_base[p+1] - 1,
 //     slot slice_base[p] + k holding its edge k (column slot_col); row_mat and
 //     row_local name the matrix and row of each position;
-//   * every per-edge message array is indexed [tile][slot][lane]: kLanes = 32
-//     frames ("lanes") are interleaved, so that one edge of a tile's frames is
-//     one contiguous 128-byte (FP32) vector. 2-byte messages (FP16/BF16) pair
-//     the tiles 2q and 2q + 1 instead: [q][slot][lane][2], so that one 32-bit
-//     word holds a lane's message in both tiles and one edge of the pair is
-//     again a 128-byte line (an odd tile count gets an unused partner);
+//   * kLanes = 32 frames ("lanes") are interleaved per tile, so that one edge
+//     of a tile's frames is one contiguous vector; the tiles 2q and 2q + 1
+//     share each message slot (an odd tile count gets an unused partner):
+//     FP32 messages as [q][slot][2][lane] (two adjacent 128-byte lines, one
+//     per tile), 2-byte messages (FP16/BF16) as [q][slot][lane][2] (one 32-bit
+//     word holds a lane's message in both tiles, one 128-byte line per edge);
+//     FP64 messages keep [tile][slot][lane] (256 bytes per edge);
 //   * col_ptr/col_slot list, for every variable node, the slots of its edges in
 //     stacked-row order (the order in which eq. (2) sums them).
 #pragma once
@@ -82,7 +83,8 @@ struct DevCode {
 // Per-call decoder state carved out of the caller's workspace.
 struct DevState {
   int32_t F, n_tiles;
-  void* c2v;          // [n_tiles][s_tot][kLanes] message type ([n_tiles / 2][s_tot][kLanes][2] for 2 bytes)
+  void* c2v;          // message type: [n_tiles / 2][s_tot][2][kLanes] (4 bytes), [n_tiles / 2][s_tot][kLanes][2]
+                      // (2 bytes), [n_tiles][s_tot][kLanes] (8 bytes); n_tiles rounded up to pairs (msg_tiles)
   void* lv;           // [n_tiles][n][kLanes] posterior L_V of eq. (2)
   void* lp;           // [n_tiles][n][kLanes] channel LLR L_P of general (LLR) inputs
   uint32_t* yt;       // [n_tiles][n] Bob's bits, bit lane, for BSC inputs; NULL when L_P comes from lp
