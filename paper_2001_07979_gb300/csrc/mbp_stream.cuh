@@ -206,10 +206,9 @@ __global__ void __launch_bounds__(256) vn_kernel(const DevCode c, const S* __res
 
 // The same update for the nodes of one degree class (DevCode::vclass_*): a
 // node and its slots are loaded together (one dependent round trip fewer), and
-// a warp takes N nodes of degree <= D so that about 16 gathers are in flight.
-// The same update for the nodes of one degree class (DevCode::vclass_*): a
-// node and its slots are loaded together (one dependent round trip fewer), and
-// a warp takes N nodes of degree <= D so that about 16 gathers are in flight.
+// a warp takes N nodes of degree <= D so that 12 to 16 gathers are in flight
+// (one tile per warp: FP64 messages and classes of more than 16 edges; the
+// other storage types take vn_class_pair_kernel).
 template <typename M, typename S, int D, int N>
 __global__ void __launch_bounds__(256) vn_class_kernel(const DevCode c, int cls, const S* __restrict__ c2v,
                                                        M* __restrict__ lv, const M* __restrict__ lp,
