@@ -145,3 +145,31 @@ def test_f32_pair_messages_odd_tiles(mbp):
         for f in (0, 31, 32, 63, 64, 69):
             c = mbp.mbp_export_c2v(codes, F, out["workspace"], f).cpu().numpy()
             assert np.max(np.abs(c - ref[f])) <= 1e-3, (t, f)
+
+
+@pytest.mark.parametrize("msg", ["f32", "f16"])
+def test_pair_kernels_on_long_rows(mbp, msg):
+    """A rate-0.8 code (check rows of about 21 edges: the pair check kernel's longest unroll bounds, 22 and 24),
+    70 frames (3 tiles, the last ragged and unpaired): streaming decodes through the pair kernels equal the
+    persistent per-edge kernels bit for bit, and converged frames equal the oracle's bits."""
+    n = 3000
+    H = mi.make_codes(n, 600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 66)
+    deg = np.concatenate([np.diff(np.asarray(h.row_ptr)) for h in H])
+    assert 18 < deg.max() <= 24
+    F = 70
+    x, y, e = mi.bsc_frames(n, F, 0.02, seed=67)  # 3 to 5 iterations per frame
+    codes = mbp.mbp_create_codes(H)
+    z = mbp.mbp_syndrome(codes, dev(i32(x)))
+    dt = MSG[msg](mbp)
+    yd, ed = dev(i32(y)), dev(e)
+    a = mbp.mbp_decode_bsc(codes, yd, ed, z, 40, msg_dtype=dt, want_soft=True, schedule=mbp.SCHED_STREAMING)
+    g = [dict(codes=codes, z_bits=z, F=F, y_bits=yd, qber=ed)]
+    mbp.mbp_multi_set_tuning(g, dict(grid_kernels=0, cn_warps=8, cn_waves=1, vn_warps=8, syn_warps=8), msg_dtype=dt)
+    b = mbp.mbp_decode_multi(g, 40, msg_dtype=dt, want_soft=True)[0]
+    torch.cuda.synchronize()
+    for k in KEYS:
+        assert torch.equal(a[k], b[k]), (msg, k)
+    ref = orc.decode(H, orc.bsc_llr(y, n, e), orc.syndrome(H, x), 40, threads=8)
+    conv = ref["success"].astype(bool) & a["success"].cpu().numpy().astype(bool)
+    assert conv.sum() >= 60
+    assert np.array_equal(a["x_hat_bits"].cpu().numpy().view(np.uint32)[conv], ref["x_hat_bits"][conv])
