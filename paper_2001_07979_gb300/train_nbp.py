@@ -1,6 +1,7 @@
 """Train the unrolled normalised BP and compare it with the plain decoder.
 
     python -m paper_2001_07979_gb300.train_nbp --steps 200 --out nbp.json
+    python -m paper_2001_07979_gb300.train_nbp --time        # forward / adjoint pass times only
 
 The learned form (mbp_nbp_forward / mbp_nbp_backward behind NormalizedBP)
 rescales every check-to-variable message of matrix l at iteration t by a
@@ -24,7 +25,8 @@ import torch
 
 import mbp_inputs as mi
 
-from . import NBPDecoder, mbp_bsc_llr, mbp_create_codes, mbp_nbp_forward, mbp_syndrome
+from . import (NBPDecoder, mbp_bsc_llr, mbp_create_codes, mbp_nbp_backward, mbp_nbp_forward,
+               mbp_nbp_workspace_size, mbp_syndrome)
 
 
 def frames(codes, n, F, qber, seed):
@@ -58,9 +60,14 @@ def main(argv=None):
     p.add_argument("--lr", type=float, default=0.01)
     p.add_argument("--eval-frames", type=int, default=1024)
     p.add_argument("--out", default=None)
+    p.add_argument("--time", action="store_true",
+                   help="only time one forward pass (T iterations, checkpoints kept) and one adjoint pass")
     args = p.parse_args(argv)
     n, m = args.n, int(round(args.n * (1 - args.rate)))
     codes = mbp_create_codes(mi.make_codes(n, m, {2: 0.3, 3: 0.4, 8: 0.3}, args.u, 4))
+    if args.time:
+        print(json.dumps(time_passes(codes, n, m, args), indent=1))
+        return 0
     dec = NBPDecoder(codes, args.T, device="cuda")
     opt = torch.optim.Adam(dec.parameters(), lr=args.lr)
     losses = []
@@ -93,6 +100,35 @@ def main(argv=None):
             f.write(text)
     print(text)
     return 0
+
+
+def time_passes(codes, n, m, args, reps=10, warmup=3):
+    """CUDA-event times of the forward pass (posteriors of all T iterations and the per-iteration message
+    checkpoints) and of the adjoint pass (gradients for alpha, beta and the LLRs) on one batch, inputs resident
+    on the GPU, after warm-up passes."""
+    llr, z, _ = frames(codes, n, args.frames, args.qber, seed=7)
+    T, u = args.T, args.u
+    alpha = torch.full((T, u), 0.9, device="cuda")
+    beta = torch.full((T, u), 0.1, device="cuda")
+    ws = torch.empty(mbp_nbp_workspace_size(codes, args.frames, T), dtype=torch.uint8, device="cuda")
+    grad = torch.randn((T, args.frames, n), device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd, bwd = [], []
+    for r in range(warmup + reps):
+        ev[0].record()
+        mbp_nbp_forward(codes, llr, z, alpha, beta, workspace=ws)
+        ev[1].record()
+        mbp_nbp_backward(codes, args.frames, alpha, beta, grad, ws, want_grad_llr=True)
+        ev[2].record()
+        torch.cuda.synchronize()
+        if r >= warmup:
+            fwd.append(ev[0].elapsed_time(ev[1]))
+            bwd.append(ev[1].elapsed_time(ev[2]))
+    f_ms, b_ms = float(np.median(fwd)), float(np.median(bwd))
+    return {"n": n, "m": m, "u": u, "T": T, "frames": args.frames, "workspace_bytes": ws.numel(),
+            "forward_ms": f_ms, "adjoint_ms": b_ms,
+            "forward_frame_iterations_per_s": args.frames * T / (f_ms / 1e3),
+            "note": "median of %d passes after %d warm-up passes, CUDA events, inputs on the GPU" % (reps, warmup)}
 
 
 def evaluate_frames(codes, L: torch.Tensor, z: torch.Tensor, F: int):
