@@ -192,6 +192,8 @@ def oracle_time(H, x, y, e, frames, threads):
     return dt, out
 
 
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (the roofline's "frac" uses the measured copy bandwidth)
+
 KERNEL_SOURCES = ("mbp_internal.h", "mbp_device.cuh", "mbp_stream.cuh", "mbp_pair.cuh", "mbp_stream_f32.cu",
                   "mbp_resident.cuh")
 
@@ -426,6 +428,8 @@ def run_gb300(args):
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_source": f"{peak_src} HBM copy bandwidth",
+                         "nominal_peak": NOMINAL_HBM_GBS,
+                         "frac_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
                          "algorithmic_bytes_per_step": b_dom, "bytes_rule": rule,
                          "launches": n_dom,
                          "mean_launch_ms": ms_dom / n_dom if n_dom else None,
