@@ -49,6 +49,17 @@ def _minsum_pin():
         var.test_minsum_bracketed_by_sum_product(d)
 
 
+def _clip_pin():
+    for u in (1, 2, 3):
+        for trial in range(3):
+            pins.test_clip_star_centre_is_map_of_clipped_leaves(u, trial)
+            pins.test_clip_chain_closed_form(u, trial)
+    for u in (1, 2):
+        for trial in range(3):
+            pins.test_clip_star_leaves_take_the_clipped_centre_extrinsic(u, trial)
+            pins.test_clip_far_away_star_posteriors_exact(u, trial)
+
+
 MUTATIONS = {
     # variable-to-check message forgets the channel prior
     "v2c_drops_prior": ("            double s = LP[i];\n            for (int64_t b",
@@ -75,6 +86,15 @@ MUTATIONS = {
     # min-sum rule ignores the syndrome bit
     "minsum_ignores_syndrome": ("    double s = z ? -1.0 : 1.0, mn = INFINITY;", "    double s = 1.0, mn = INFINITY;",
                                 _minsum_pin),
+    # variable-to-check messages not clipped before eq. (6)
+    "v2c_no_clip": ("v2c[a] = clip(s, L);", "v2c[a] = s;", _clip_pin),
+    # variable-to-check clip at half the bound
+    "v2c_clip_half": ("v2c[a] = clip(s, L);", "v2c[a] = clip(s, 0.5 * L);", _clip_pin),
+    # variable-to-check clip at a fixed 20 instead of the L_max given
+    "v2c_clip_fixed": ("v2c[a] = clip(s, L);", "v2c[a] = clip(s, 20.0);", _clip_pin),
+    # check-to-variable messages of the decoder not clipped after eq. (6) (a degree-1 check then sends inf)
+    "decode_c2v_no_clip": ("else if (orc_check_node(d, vin, zj, L, vout)) return -2;",
+                           "else if (orc_check_node(d, vin, zj, INFINITY, vout)) return -2;", _clip_pin),
     # eq. (5) with P^0 and P^1 swapped
     "llr_orientation": ("L_P[i] = log(p0 / p1);", "L_P[i] = log(p1 / p0);", _llr_pin),
 }

@@ -327,3 +327,191 @@ def test_loopy_tiny_codes_invariants_and_ml_bound():
             bp_err += int(not (out["success"][0] and np.array_equal(xh, x[0])))
             trials += 1
     assert bp_err >= ml_err - 3 * math.sqrt(trials * 0.25)
+
+
+# ------------------------------------- message clip inside whole decodes
+#
+# The paper has no guard against atanh(+-1) or message growth (eq. 6); the
+# decoder clips every variable-to-check message to [-L_max, L_max] before eq. (6)
+# and every check-to-variable message after it, so that an empty combination
+# (a degree-1 check, +inf) becomes +-L_max. These cases pin that reading inside
+# whole decodes, on codes where the clip is reached, against enumeration and
+# closed forms that do not run the oracle's message passing.
+
+def _star(K, u, deg1_matrix, rng, L, group=(1, 2)):
+    """Centre variable 0 and K leaf groups: group k (one or two fresh leaves, sizes cycling through `group`) is
+    joined to the centre by one check of matrix k % u (degree 2 or 3), plus one degree-1 check on the centre in
+    matrix `deg1_matrix`. Leaf priors reach up to 3 L. Returns n, the dense matrices, syndromes, priors and
+    the leaves of each group."""
+    n, leaves = 1, []
+    for k in range(K):
+        g = group[k % len(group)]
+        leaves.append(list(range(n, n + g)))
+        n += g
+    rows = [[] for _ in range(u)]
+    for k in range(K):
+        rows[k % u].append([0] + leaves[k])
+    rows[deg1_matrix].append([0])
+    dens = []
+    for l in range(u):
+        h = np.zeros((len(rows[l]), n), np.uint8)
+        for j, c in enumerate(rows[l]):
+            h[j, c] = 1
+        dens.append(h)
+    zs = [rng.integers(0, 2, size=h.shape[0]).astype(np.uint8) for h in dens]
+    LP = np.empty(n)
+    LP[0] = rng.uniform(-1.0, 1.0)
+    LP[1:] = rng.choice([-1.0, 1.0], size=n - 1) * rng.uniform(0.3 * L, 3.0 * L, size=n - 1)
+    return n, dens, zs, LP, leaves
+
+
+def _map_llr_from_priors(dens, zs, LP, i):
+    """ln P(x_i = 0 | checks) / P(x_i = 1 | checks) for independent priors of LLR LP, by enumeration."""
+    n = len(LP)
+    X = ((np.arange(2 ** n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int64)
+    ok = np.ones(2 ** n, bool)
+    for h, z in zip(dens, zs):
+        if h.shape[0]:
+            ok &= np.all((X @ h.T.astype(np.int64)) % 2 == z[None, :].astype(np.int64), axis=1)
+    # log P(x) up to a constant: sum over bits of -LP_k x_k (LLR = ln P(0)/P(1))
+    logw = -(X[ok] * LP[None, :]).sum(axis=1)
+    w = np.exp(logw - logw.max())
+    Xo = X[ok]
+    return math.log(w[Xo[:, i] == 0].sum() / w[Xo[:, i] == 1].sum())
+
+
+def _replace_degree1_by_aux(dens, L):
+    """A degree-1 check on x_i with syndrome z is, after the clip, the message (-1)^z L_max: the same as a
+    degree-2 check (x_i, a) with syndrome z on a fresh variable a of prior +L_max. Returns the extended
+    matrices and the number of auxiliary variables (appended after the code's own)."""
+    n = dens[0].shape[1]
+    n_aux = sum(int((h.sum(axis=1) == 1).sum()) for h in dens)
+    out, a = [], n
+    for h in dens:
+        g = np.zeros((h.shape[0], n + n_aux), np.uint8)
+        g[:, :n] = h
+        for j in range(h.shape[0]):
+            if h[j].sum() == 1:
+                g[j, a] = 1
+                a += 1
+        out.append(g)
+    return out, n_aux
+
+
+@pytest.mark.parametrize("u", [1, 2, 3])
+@pytest.mark.parametrize("trial", range(3))
+def test_clip_star_centre_is_map_of_clipped_leaves(u, trial):
+    """Centre of a star: after any iteration t >= 1 each leaf check sends eq. (6) of its leaves' clipped priors
+    (a leaf has no other check) and the degree-1 check (-1)^z L_max, so the centre's posterior is the exact
+    bitwise MAP of the same code with every leaf prior clipped to L_max and the degree-1 check replaced by an
+    auxiliary variable of prior L_max. On the degree-3 leaf checks the clip before eq. (6) decides the message
+    (on degree-2 ones the clip after it would give the same)."""
+    rng = np.random.default_rng(7000 + 10 * u + trial)
+    L = 4.0
+    n, dens, zs, LP, _ = _star(6, u, trial % u, rng, L)
+    assert np.max(np.abs(LP)) > L, "case must reach the clip"
+    H = [csr_from_dense(h) for h in dens]
+    for T in (1, 2, 5):
+        out = orc.decode(H, LP[None, :], z_bits_from_dense(zs), T, l_max=L, early_exit=False, want_lv=True)
+        ext, n_aux = _replace_degree1_by_aux(dens, L)
+        LPc = np.concatenate([[LP[0]], np.clip(LP[1:], -L, L), np.full(n_aux, L)])
+        ref = _map_llr_from_priors(ext, zs, LPc, 0)
+        assert out["L_V"][0, 0] == pytest.approx(ref, abs=1e-12), (T, out["L_V"][0, 0], ref)
+
+
+@pytest.mark.parametrize("u", [1, 2])
+@pytest.mark.parametrize("trial", range(3))
+def test_clip_star_leaves_take_the_clipped_centre_extrinsic(u, trial):
+    """A leaf of a star from iteration 2 on: its only check k sends it the LLR of the XOR of the check's other
+    bits (eq. 6, by enumeration) given the clipped message of each: clip(E_k, L_max) from the centre, where E_k
+    is the MAP LLR of the centre in the code without check k (leaf priors clipped, degree-1 check as an
+    auxiliary variable of prior L_max; enumeration), and clip(L_P, L_max) from the other leaf of a degree-3
+    check. The centre's message exceeds L_max here, so the clip before eq. (6) decides the result."""
+    rng = np.random.default_rng(7100 + 10 * u + trial)
+    L = 3.0
+    n, dens, zs, LP, leaves = _star(6, u, 0, rng, L)
+    H = [csr_from_dense(h) for h in dens]
+    out = orc.decode(H, LP[None, :], z_bits_from_dense(zs), 4, l_max=L, early_exit=False, want_lv=True)
+    ext, n_aux = _replace_degree1_by_aux(dens, L)
+    LPc = np.concatenate([[LP[0]], np.clip(LP[1:], -L, L), np.full(n_aux, L)])
+    reached = 0
+    for k, grp in enumerate(leaves):
+        l = k % u
+        j = int(np.nonzero(dens[l][:, grp[0]])[0][0])
+        without = [g if q != l else np.delete(g, j, axis=0) for q, g in enumerate(ext)]
+        zw = [z if q != l else np.delete(z, j) for q, z in enumerate(zs)]
+        E = _map_llr_from_priors(without, zw, LPc, 0)
+        reached += abs(E) > L
+        for a in grp:
+            others = [float(np.clip(E, -L, L))] + [float(np.clip(LP[b], -L, L)) for b in grp if b != a]
+            ref = LP[a] + (-1) ** int(zs[l][j]) * xor_llr_enumerated(others)
+            assert out["L_V"][0, a] == pytest.approx(ref, abs=1e-12), (a, out["L_V"][0, a], ref)
+    assert reached >= 1, "case must reach the variable-to-check clip"
+
+
+def _chain(K, u, rng, L):
+    """Path x_0 - x_1 - ... - x_{K-1}: check j joins (x_j, x_{j+1}) in matrix j % u; a degree-1 check on x_0
+    in matrix 0."""
+    rows = [[] for _ in range(u)]
+    for j in range(K - 1):
+        rows[j % u].append((j, [j, j + 1]))
+    rows[0].append((-1, [0]))
+    dens, where = [], {}
+    for l in range(u):
+        h = np.zeros((len(rows[l]), K), np.uint8)
+        for r, (j, c) in enumerate(rows[l]):
+            h[r, c] = 1
+            where[j] = (l, r)
+        dens.append(h)
+    zs = [rng.integers(0, 2, size=h.shape[0]).astype(np.uint8) for h in dens]
+    LP = rng.choice([-1.0, 1.0], size=K) * rng.uniform(0.2 * L, 2.5 * L, size=K)
+    return dens, zs, LP, where
+
+
+@pytest.mark.parametrize("u", [1, 2, 3])
+@pytest.mark.parametrize("trial", range(3))
+def test_clip_chain_closed_form(u, trial):
+    """On a path every check has degree 2 (it passes the other side's message with the sign of its syndrome
+    bit) and every variable at most two checks, so the message entering x_i from the left is
+    a_i = s_{i-1} clip(L_P,{i-1} + a_{i-1}, L_max) with a_0 the degree-1 check's s L_max, the one from the
+    right b_i = s_i clip(L_P,{i+1} + b_{i+1}, L_max) with b_{K-1} = 0, and after K iterations (the flooding
+    messages have then crossed the whole path) the posterior is L_P,i + a_i + b_i."""
+    rng = np.random.default_rng(7200 + 10 * u + trial)
+    L, K = 3.0, 10
+    dens, zs, LP, where = _chain(K, u, rng, L)
+    H = [csr_from_dense(h) for h in dens]
+    out = orc.decode(H, LP[None, :], z_bits_from_dense(zs), K + 2, l_max=L, early_exit=False, want_lv=True)
+
+    def sign(j):
+        l, r = where[j]
+        return -1.0 if zs[l][r] else 1.0
+
+    a = np.zeros(K)
+    a[0] = sign(-1) * L
+    for i in range(1, K):
+        a[i] = sign(i - 1) * min(max(LP[i - 1] + a[i - 1], -L), L)
+    b = np.zeros(K)
+    for i in range(K - 2, -1, -1):
+        b[i] = sign(i) * min(max(LP[i + 1] + b[i + 1], -L), L)
+    assert np.any(np.abs(LP[:-1] + a[:-1]) > L) and np.any(np.abs(LP[1:] + b[1:]) > L), "case must reach the clip"
+    assert np.allclose(out["L_V"][0], LP + a + b, atol=1e-12, rtol=0), (out["L_V"][0], LP + a + b)
+
+
+@pytest.mark.parametrize("u", [1, 2])
+@pytest.mark.parametrize("trial", range(3))
+def test_clip_far_away_star_posteriors_exact(u, trial):
+    """The clip is only a bound: on a star (a tree) whose exact MAP posteriors exceed 20 in magnitude, a decode
+    with L_max far above every message gives the exact bitwise MAP posterior of every variable (enumeration of
+    the unclipped problem), as a decode inside the clip does."""
+    rng = np.random.default_rng(7300 + 10 * u + trial)
+    n, dens, zs, LP, _ = _star(6, u, 0, rng, 5.0, group=(1,))
+    dens = [h[h.sum(axis=1) > 1] for h in dens]  # no degree-1 check: its unclipped message is infinite
+    x = rng.integers(0, 2, size=n)  # priors that mostly agree with a word of the code, as a channel's do
+    zs = [((h.astype(np.int64) @ x) % 2).astype(np.uint8) for h in dens]
+    LP = (1.0 - 2.0 * x) * np.abs(LP)
+    LP[1] = -LP[1]
+    ref = np.array([_map_llr_from_priors(dens, zs, LP, i) for i in range(n)])
+    assert np.max(np.abs(ref)) > 20.0, "case must leave the default clip"
+    H = [csr_from_dense(h) for h in dens]
+    out = orc.decode(H, LP[None, :], z_bits_from_dense(zs), 3, l_max=1e4, early_exit=False, want_lv=True)
+    assert np.allclose(out["L_V"][0], ref, atol=1e-9, rtol=1e-12), (out["L_V"][0], ref)
