@@ -24,10 +24,17 @@
  *  - Syndromes of F frames are laid out [u][F][ceil(m_l/32)]: all frames of
  *    matrix 1, then all frames of matrix 2, and so on.
  *  - LLRs are ln(P(bit = 0) / P(bit = 1)) (positive favours 0).
- *  - Work is issued on `stream` (NULL = the legacy default stream).
- *    mbp_syndrome and mbp_bsc_llr are asynchronous. The decode calls read a
- *    per-iteration count of unfinished frames back to the host, so they return
- *    only when decoding has finished on `stream`.
+ *  - Work is issued on `stream` (NULL = the legacy default stream) and is
+ *    stream-ordered. mbp_syndrome, mbp_bsc_llr, the NBP calls and the decode
+ *    calls under the graph schedule (the default wherever it applies, see
+ *    MBP_SCHED_AUTO) are asynchronous: they return once the work is queued, and
+ *    the outputs are ready when `stream` reaches that point. The streaming and
+ *    resident schedules read state back to the host during the call and return
+ *    when decoding has finished; so do mbp_decode_bsc_host (it copies the
+ *    outputs to host memory), mbp_autotune_multi, opts->validate = 1 (one
+ *    read-back of the non-finite check) and kernel accounting.
+ *  - Device pointers and the codes handle must belong to the device that is
+ *    current when the call is made; a mismatch is MBP_EINVAL.
  */
 #ifndef MBP_H
 #define MBP_H
@@ -91,15 +98,23 @@ enum { MBP_ACC_AUTO = 0, MBP_ACC_FLOAT = 1, MBP_ACC_FIXED = 2 };
  *                       point accumulation and FP32 or FP64 storage. A barrier
  *                       that waits longer than about 2 s ends the decode with
  *                       MBP_ETIMEOUT;
- *  MBP_SCHED_GRAPH      the schedule of mbp_decode_multi with one group:
- *                       persistent kernels over a device-built list of the
- *                       unfinished tiles, the iteration loop inside a CUDA
- *                       graph (a WHILE node that the retirement kernel drives),
- *                       so no host round trip per iteration; FP32, FP16 or
- *                       BF16 storage, floating-point accumulation. The
- *                       workspace layout differs (size it with this schedule);
- *  MBP_SCHED_AUTO       (default) STREAMING, which measures faster on GB300
- *                       for the benchmark workload.
+ *  MBP_SCHED_GRAPH      the schedule of mbp_decode_multi with one group: the
+ *                       streaming schedule's kernels (or, if mbp_autotune_multi
+ *                       chose them, persistent kernels over a device-built list
+ *                       of the unfinished tiles) with the iteration loop inside
+ *                       a CUDA graph (a WHILE node that the retirement kernel
+ *                       drives), so no host round trip per iteration and the
+ *                       call returns once the work is queued; FP32, FP16 or
+ *                       BF16 storage, floating-point accumulation, flooding
+ *                       sum-product. The workspace layout differs from the
+ *                       other schedules' (size it with the same opts). The
+ *                       graph is built on the first call for each workspace,
+ *                       frame count and input kind and then cached (at most
+ *                       16; destroying a code drops the graphs that name it);
+ *  MBP_SCHED_AUTO       (default) GRAPH where it applies (flooding sum-product
+ *                       with FP32, FP16 or BF16 storage and floating-point
+ *                       accumulation), STREAMING otherwise (FP64 storage,
+ *                       fixed-point accumulation, min-sum, matrix-serial).
  */
 enum { MBP_SCHED_AUTO = 0, MBP_SCHED_STREAMING = 1, MBP_SCHED_RESIDENT = 2, MBP_SCHED_GRAPH = 3 };
 
@@ -118,8 +133,8 @@ enum { MBP_SCHED_AUTO = 0, MBP_SCHED_STREAMING = 1, MBP_SCHED_RESIDENT = 2, MBP_
  *                           eq. (2), then H_2's checks (reading that posterior)
  *                           and eq. (2), and so on; the stopping rule after all
  *                           u matrices.
- * Both variants run with the streaming schedule (AUTO or STREAMING) and
- * floating-point accumulation.
+ * Both variants run with the streaming schedule (AUTO, which then means
+ * STREAMING, or STREAMING) and floating-point accumulation.
  */
 enum { MBP_RULE_SUM_PRODUCT = 0, MBP_RULE_MIN_SUM = 1 };
 enum { MBP_UPDATE_FLOODING = 0, MBP_UPDATE_MATRIX_SERIAL = 1 };
@@ -214,7 +229,9 @@ int mbp_decode_workspace_size(const mbp_codes* codes, int F, const mbp_opts* opt
  * (0 if the input already satisfied every syndrome, max_iter on failure);
  * success [F] = 1 iff the output satisfies every syndrome within max_iter.
  * On failure the output is the hard decision of the last iteration.
- * opts may be NULL only when F == 0. Blocks until the decode has finished.
+ * opts may be NULL only when F == 0. Asynchronous under the graph schedule
+ * (the default for FP32, FP16 and BF16 storage); the streaming and resident
+ * schedules return when the decode has finished.
  */
 int mbp_decode_batch(const mbp_codes* codes, int F, const void* llr, const uint32_t* z_bits, int max_iter,
                      const mbp_opts* opts, uint32_t* x_hat_bits, int32_t* iters, uint8_t* success,
@@ -379,13 +396,19 @@ int mbp_nbp_backward(const mbp_codes* codes, int F, int T, const float* alpha, c
  * device array of MBP_STATIC_SCRATCH_BYTES inside this library instead of
  * opts->workspace. opts->workspace and opts->workspace_bytes are ignored, and
  * opts->host_io must be 0; opts->schedule MBP_SCHED_GRAPH gives MBP_EUNSUPPORTED
- * (instantiating a graph may allocate). The call allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library routine.
+ * (instantiating a graph may allocate), and MBP_SCHED_AUTO runs the streaming
+ * schedule, so the call returns when decoding has finished. opts->validate has
+ * no effect here (BSC inputs carry no LLR array to check). The call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *  - The array is created when the library's device code is loaded on a GPU.
  *    Every GPU that loads the library holds it until the process exits.
- *  - The first call on each device looks up the array's device address, with
- *    that device current, and caches it. Make that first call before starting
- *    any stream capture.
+ *  - The array's device address is looked up once per device, with that device
+ *    current, and cached. mbp_create_codes does this for the device it uploads
+ *    to (which also loads the library's device code there), so the
+ *    allocation-free calls that use those codes neither load code nor look the
+ *    address up. Should that look-up have failed, the first allocation-free
+ *    call on the device repeats it: make that call before starting any stream
+ *    capture.
  *  - Sizes: a batch whose workspace (mbp_decode_workspace_size with the same
  *    opts) exceeds MBP_STATIC_SCRATCH_BYTES is rejected with MBP_EINVAL.
  *  - Every call shares the one array and leaves its contents behind. The

@@ -29,6 +29,8 @@ int cuda_error(cudaError_t e, const char* what) {
   return set_error(MBP_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+// Device or managed memory that the current device's kernels may address: device memory must belong to the
+// current device (the kernels of a decode run there); managed memory migrates on access.
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -37,7 +39,24 @@ static bool is_device_ptr(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == cur;
+}
+
+// The device that is current for this host thread, or -1.
+static int current_device() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return d;
 }
 
 // ---- kernel accounting (mbp_profile_*)
@@ -128,6 +147,18 @@ namespace {
 #define REQUIRE_DEV(p, name) \
   REQUIRE(is_device_ptr(p), "%s must be a device pointer of the current device", name)
 
+#define REQUIRE_CODES_HERE(c)                                                                              \
+  REQUIRE((c)->device == current_device(), "codes were uploaded to device %d, but device %d is current", \
+          (c)->device, current_device())
+
+// MBP_SCHED_AUTO takes the graph schedule wherever it runs the options (flooding sum-product, FP32, FP16 or
+// BF16 storage, floating-point accumulation), else the streaming schedule.
+bool graph_schedule(const mbp_opts* o) {
+  if (o->schedule == MBP_SCHED_GRAPH) return true;
+  return o->schedule == MBP_SCHED_AUTO && o->rule == MBP_RULE_SUM_PRODUCT && o->update == MBP_UPDATE_FLOODING &&
+         o->msg_dtype != MBP_MSG_F64 && o->accumulate != MBP_ACC_FIXED;
+}
+
 int validate_opts(const mbp_opts* o) {
   REQUIRE(o, "opts is NULL");
   REQUIRE(o->msg_dtype == MBP_MSG_F32 || o->msg_dtype == MBP_MSG_F64 || o->msg_dtype == MBP_MSG_F16 ||
@@ -165,7 +196,7 @@ mbp_group one_group(const mbp_codes* c, int F) {
 }
 
 int single_workspace(const mbp_codes* c, int F, const mbp_opts* o, bool host_io, size_t* need) {
-  if (o->schedule != MBP_SCHED_GRAPH) {
+  if (!graph_schedule(o)) {
     *need = workspace_bytes(c->d, F, o->msg_dtype, host_io);
     return MBP_OK;
   }
@@ -175,7 +206,7 @@ int single_workspace(const mbp_codes* c, int F, const mbp_opts* o, bool host_io,
 
 // The decoder state of a single-code decode inside its workspace.
 int single_state(const mbp_codes* c, int F, const mbp_opts* o, bool host_io, void* ws, DevState* st) {
-  if (o->schedule != MBP_SCHED_GRAPH) {
+  if (!graph_schedule(o)) {
     carve_workspace(c->d, F, o->msg_dtype, host_io, ws, st);
     return MBP_OK;
   }
@@ -201,6 +232,7 @@ int common_decode_checks(const mbp_codes* codes, int F, int max_iter, const mbp_
   REQUIRE(F >= 0, "F must be >= 0");
   REQUIRE(max_iter >= 0 && max_iter <= 1000000, "max_iter must be in [0, 1e6]");
   if (F == 0) return MBP_OK;
+  REQUIRE_CODES_HERE(codes);
   int rc = validate_opts(opts);
   if (rc) return rc;
   return check_workspace(codes, F, opts);
@@ -417,6 +449,15 @@ int mbp_create_codes(const mbp_csr* H, int u, mbp_codes** out) {
   d.vrow = m_tot < (int64_t(1) << 25) ? reinterpret_cast<const int32_t*>(base + parts[11].off) : nullptr;
   d.row_at = reinterpret_cast<const int32_t*>(base + parts[12].off);
   h->d = d;
+  // The allocation-free decode's scratch lives in this library's device code; looking its address up here,
+  // where allocating is allowed, loads that code on this device (lazy module loading would otherwise do so
+  // inside the first allocation-free call).
+  // A failure here is not the upload's: the allocation-free call repeats the look-up and reports it.
+  void* scratch = nullptr;
+  if (static_scratch(&scratch) != MBP_OK) {
+    cudaGetLastError();
+    g_err.clear();
+  }
   *out = h;
   return MBP_OK;
 }
@@ -450,6 +491,7 @@ int mbp_syndrome(const mbp_codes* codes, const uint32_t* x_bits, int F, uint32_t
   REQUIRE(codes, "codes is NULL");
   REQUIRE(F >= 0, "F must be >= 0");
   if (F == 0) return MBP_OK;
+  REQUIRE_CODES_HERE(codes);
   REQUIRE_DEV(x_bits, "x_bits");
   REQUIRE_DEV(z_bits, "z_bits");
   cudaError_t e = launch_syndrome(codes->d, x_bits, F, z_bits, reinterpret_cast<cudaStream_t>(stream));
@@ -494,7 +536,7 @@ static int decode_common(const mbp_codes* codes, int F, const void* llr, const u
   REQUIRE_DEV(success, "success");
   if (opts->soft_out) REQUIRE_DEV(opts->soft_out, "opts->soft_out");
   if (opts->synd_ok) REQUIRE_DEV(opts->synd_ok, "opts->synd_ok");
-  if (opts->schedule == MBP_SCHED_GRAPH) {
+  if (graph_schedule(opts)) {
     mbp_group g = one_group(codes, F);
     g.llr = llr;
     g.y_bits = y_bits;
@@ -587,7 +629,7 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   a.success = st.io_success;
   a.soft_out = opts->soft_out;
   a.synd_ok = opts->synd_ok;
-  if (opts->schedule == MBP_SCHED_GRAPH) {
+  if (graph_schedule(opts)) {
     mbp_group g = one_group(codes, F);
     g.y_bits = st.io_y;
     g.qber = st.io_qber;
@@ -620,8 +662,9 @@ int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits,
   if (F == 0) return MBP_OK;
   int rc = validate_opts(opts);
   if (rc) return rc;
+  REQUIRE_CODES_HERE(codes);
   REQUIRE(opts->host_io == 0, "opts->host_io must be 0 for mbp_decode_bsc_static");
-  if (opts->schedule == MBP_SCHED_GRAPH)  // instantiating a CUDA graph may allocate
+  if (opts->schedule == MBP_SCHED_GRAPH)  // instantiating a CUDA graph may allocate; AUTO runs the streaming one
     return set_error(MBP_EUNSUPPORTED, "mbp_decode_bsc_static runs the streaming or resident schedule only");
   const size_t need = workspace_bytes(codes->d, F, opts->msg_dtype, false);
   REQUIRE(need <= MBP_STATIC_SCRATCH_BYTES,
@@ -666,6 +709,7 @@ int mbp_export_c2v(const mbp_codes* codes, int F, const mbp_opts* opts, int fram
   g_err.clear();
   REQUIRE(codes, "codes is NULL");
   REQUIRE(F > 0 && frame >= 0 && frame < F, "frame %d outside [0, F = %d)", frame, F);
+  REQUIRE_CODES_HERE(codes);
   int rc = validate_opts(opts);
   if (rc) return rc;
   rc = check_workspace(codes, F, opts);
@@ -688,6 +732,7 @@ static int check_groups(const mbp_group* g, int G, const mbp_opts* o, bool need_
   for (int i = 0; i < G; ++i) {
     REQUIRE(g[i].codes, "group %d: codes is NULL", i);
     REQUIRE(g[i].F >= 0, "group %d: F must be >= 0", i);
+    if (need_workspace && g[i].F > 0) REQUIRE_CODES_HERE(g[i].codes);
     tiles += (g[i].F + kLanes - 1) / kLanes;
   }
   if (tiles > 65535) return set_error(MBP_EUNSUPPORTED, "a batch may hold at most %d frames", 65535 * kLanes);
@@ -766,6 +811,7 @@ static int check_nbp(const mbp_codes* codes, int F, int T, double l_max, const v
   if (codes->d.max_row_deg > 32)
     return set_error(MBP_EUNSUPPORTED, "the unrolled decoder supports checks of at most 32 edges");
   if (F == 0) return MBP_OK;
+  REQUIRE_CODES_HERE(codes);
   if ((F + kLanes - 1) / kLanes > 65535) return set_error(MBP_EUNSUPPORTED, "F = %d is too large", F);
   const size_t need = nbp_workspace_bytes(codes->d, F, T);
   REQUIRE(ws, "workspace is NULL (size it with mbp_nbp_workspace_size)");

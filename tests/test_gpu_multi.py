@@ -209,7 +209,7 @@ def test_graph_schedule_single_code_entries(mbp, batch):
     for k in KEYS:
         assert torch.equal(a[k], b[k]), k
     for f in (0, g.F - 1):
-        ca = mbp.mbp_export_c2v(g.codes, g.F, a["workspace"], f)
+        ca = mbp.mbp_export_c2v(g.codes, g.F, a["workspace"], f, schedule=mbp.SCHED_STREAMING)
         cb = mbp.mbp_export_c2v(g.codes, g.F, b["workspace"], f, schedule=mbp.SCHED_GRAPH)
         assert torch.equal(ca, cb)
     z_host = g.z.cpu().numpy().view(np.uint32)

@@ -143,7 +143,7 @@ def test_f32_pair_messages_odd_tiles(mbp):
                                    schedule=mbp.SCHED_STREAMING)
         ref = orc.decode(H, LP, orc.syndrome(H, x), t, early_exit=False, want_c2v=True)["c2v"]
         for f in (0, 31, 32, 63, 64, 69):
-            c = mbp.mbp_export_c2v(codes, F, out["workspace"], f).cpu().numpy()
+            c = mbp.mbp_export_c2v(codes, F, out["workspace"], f, schedule=mbp.SCHED_STREAMING).cpu().numpy()
             assert np.max(np.abs(c - ref[f])) <= 1e-3, (t, f)
 
 

@@ -100,7 +100,8 @@ def test_bsc_llr_matches_oracle(mbp):
 
 # ------------------------------------------------------- whole decoder
 
-MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident", "f16", "bf16", "f32-graph", "f16-graph"]
+MODES = ["f64", "f32-float", "f32-fixed", "f64-resident", "f32-resident", "f16", "bf16", "f32-graph", "f16-graph",
+         "bf16-graph", "f32-default"]
 
 
 def mode_args(mbp, mode):
@@ -113,9 +114,13 @@ def mode_args(mbp, mode):
     if mode == "f64-resident":
         return dict(msg_dtype=mbp.MSG_F64, schedule=mbp.SCHED_RESIDENT)
     if mode == "f16":
-        return dict(msg_dtype=mbp.MSG_F16)
+        return dict(msg_dtype=mbp.MSG_F16, schedule=mbp.SCHED_STREAMING)
     if mode == "bf16":
-        return dict(msg_dtype=mbp.MSG_BF16)
+        return dict(msg_dtype=mbp.MSG_BF16, schedule=mbp.SCHED_STREAMING)
+    if mode == "bf16-graph":
+        return dict(msg_dtype=mbp.MSG_BF16, schedule=mbp.SCHED_GRAPH)
+    if mode == "f32-default":  # the default options: AUTO, which is the graph schedule for FP32 messages
+        return dict(msg_dtype=mbp.MSG_F32, schedule=mbp.SCHED_AUTO)
     if mode == "f32-graph":
         return dict(msg_dtype=mbp.MSG_F32, schedule=mbp.SCHED_GRAPH)
     if mode == "f16-graph":
@@ -128,6 +133,7 @@ def mode_args(mbp, mode):
 # the first iteration. Later iterations carry these differences on; their size is reported, not bounded.
 STORE_ROUNDOFF = {"f16": 2.0 ** -11 * 32.0 * 0.6931471805599453, "bf16": 2.0 ** -8 * 32.0 * 0.6931471805599453}
 STORE_ROUNDOFF["f16-graph"] = STORE_ROUNDOFF["f16"]
+STORE_ROUNDOFF["bf16-graph"] = STORE_ROUNDOFF["bf16"]
 
 
 def tolerance(mode, t, max_col_deg):
@@ -200,7 +206,8 @@ def test_rate07_n65536_first_iterations_fp32(mbp, mode):
         ref = orc.decode(w.H, LP, w.z_orc, t, early_exit=False, want_lv=True, want_c2v=True, threads=3)
         assert np.max(np.abs(out["soft"].cpu().numpy() - ref["L_V"])) <= TOL_F32
         for f in range(w.F):
-            c = mbp.mbp_export_c2v(codes, w.F, out["workspace"], f).cpu().numpy()
+            c = mbp.mbp_export_c2v(codes, w.F, out["workspace"], f,
+                                   schedule=mode_args(mbp, mode)["schedule"]).cpu().numpy()
             assert np.max(np.abs(c - ref["c2v"][f])) <= TOL_F32
 
 

@@ -94,7 +94,7 @@ def test_row_form_export_after_one_and_two_iterations(mbp):
                                  schedule=mbp.SCHED_STREAMING)
         ref = orc.decode(H, orc.bsc_llr(y, n, e), orc.syndrome(H, x), t, early_exit=False, want_c2v=True)["c2v"]
         for f in (0, 17, 39):
-            c = mbp.mbp_export_c2v(codes, F, out["workspace"], f).cpu().numpy()
+            c = mbp.mbp_export_c2v(codes, F, out["workspace"], f, schedule=mbp.SCHED_STREAMING).cpu().numpy()
             assert np.max(np.abs(c - ref[f])) <= 1e-3, (t, f)
 
 
