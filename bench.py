@@ -602,14 +602,36 @@ def run_uneven(args):
 
     ms_single, outs_single = timed(step_single)
     same = all(torch.equal(a[k], b[k]) for a, b in zip(outs, outs_single) for k in ("x_hat_bits", "iters", "success"))
+    # per-family device times of one grouped decode (kernel accounting drives the same kernels from the host)
+    mbp.mbp_profile_enable(True)
+    step()
+    torch.cuda.synchronize()
+    prof = mbp.mbp_profile_get()
+    mbp.mbp_profile_enable(False)
     fails = undetected = 0
     it_sum = 0
-    for o, x in zip(outs, xs):
+    failing, per_group = [], []
+    for sp, o, x, g in zip(specs, outs, xs, groups):
         ok = o["success"].cpu().numpy().astype(bool)
         xh = o["x_hat_bits"].cpu().numpy().view(np.uint32)
+        it = o["iters"].cpu().numpy()
         fails += int((~ok).sum())
         undetected += int(np.sum(ok & ~np.all(xh == x, axis=1)))
-        it_sum += int(o["iters"].sum().item())
+        it_sum += int(it.sum())
+        h = lambda q: -q * np.log2(q) - (1 - q) * np.log2(1 - q)
+        for f in np.flatnonzero(~ok):
+            q = float(sp["qber"][f])
+            failing.append({"n": sp["n"], "rate": sp["rate"], "u": sp["u"], "qber": q, "iters": int(it[f]),
+                            "f": sp["m"] / (sp["n"] * h(q)), "f_leak": sp["u"] * sp["m"] / (sp["n"] * h(q))})
+        if sp["frames"]:
+            # work in edge x frame x iteration units: per frame as run, and as a tile pair (64 frames) costs,
+            # since the kernels move a pair's messages until its last frame has stopped
+            e_tot = g["codes"].edges
+            pair_max = [int(it[q:q + 64].max()) for q in range(0, it.size, 64)]
+            per_group.append({"n": sp["n"], "rate": sp["rate"], "u": sp["u"], "frames": sp["frames"],
+                              "mean_iterations": float(it.mean()), "max_iterations": int(it.max()),
+                              "edge_frame_iterations": int(e_tot) * int(it.sum()),
+                              "edge_frame_iterations_per_pair": int(e_tot) * 64 * int(sum(pair_max))})
     line = {
         "metric": METRIC, "value": bits / (ms / 1e3) / 1e6, "unit": "Mbps", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -619,6 +641,12 @@ def run_uneven(args):
                    "tuning": tuning, "l2": "per-step decoder state of several GB > 129 MB L2 (no flush)"},
         "single_code_calls": {"ms_per_step": ms_single, "value": bits / (ms_single / 1e3) / 1e6,
                               "outputs_identical": same},
+        "failing_frames": failing, "groups": per_group,
+        "work_rate": {"edge_frame_iterations_per_s": sum(g["edge_frame_iterations"] for g in per_group) / (ms / 1e3),
+                      "pair_granularity_per_s": sum(g["edge_frame_iterations_per_pair"] for g in per_group)
+                      / (ms / 1e3)},
+        "kernel_ms": {k: v[1] for k, v in prof.items()},
+        "kernel_ms_source": "one grouped decode with a CUDA event pair around every kernel launch (host-driven loop)",
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

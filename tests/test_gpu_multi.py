@@ -317,3 +317,72 @@ def test_graph_cache_keys_on_inputs_and_forgets_freed_codes(mbp, batch):
         for k in ("x_hat_bits", "iters", "success"):
             assert torch.equal(og[k], os_[k]), (seed, k)
         del codes, og, os_
+
+
+@pytest.mark.slow
+def test_multi_config4_sizes_match_oracle(mbp):
+    """Codes of the 4096-frame uneven workload at full size (n = 2^14, 2^16, 2^18; rates 0.5 and 0.8; u = 2
+    and 3), five frames of each with the workload's own QBERs, decoded in one grouped call (default launch
+    shapes, after autotuning, and with the persistent list kernels): output bits, success flags and per-matrix
+    syndrome flags equal the FP64
+    oracle's on every frame the oracle decodes, and every reported success satisfies all syndromes."""
+    specs = mi.uneven_batch(4096, 4)
+    pick = [(65536, 0.5, 3), (65536, 0.8, 2), (262144, 0.5, 2), (262144, 0.8, 3), (16384, 0.8, 2)]
+    groups = []
+    for key in pick:
+        sp = next(s for s in specs if (s["n"], s["rate"], s["u"]) == key)
+        H = mi.make_codes(sp["n"], sp["m"], sp["dist"], sp["u"], sp["cfg_seed"])
+        x, y, e = mi.bsc_frames(sp["n"], sp["frames"], sp["qber"], seed=sp["cfg_seed"])
+        x, y, e = x[:5], y[:5], e[:5]
+        codes = mbp.mbp_create_codes(H)
+        groups.append(dict(H=H, x=x, y=y, e=e, n=sp["n"],
+                           arg=dict(codes=codes, y_bits=dev(i32(y)), qber=dev(e),
+                                    z_bits=mbp.mbp_syndrome(codes, dev(i32(x))))))
+    args = [g["arg"] for g in groups]
+    runs = [mbp.mbp_decode_multi(args, 60, want_synd=True)]
+    runs.append(mbp.mbp_autotune_multi(args, 60)[0])
+    # and the persistent list kernels over the frames of all groups, whichever shape the autotuner kept
+    mbp.mbp_multi_set_tuning(args, dict(grid_kernels=0, cn_warps=8, cn_waves=1, vn_warps=8, syn_warps=8))
+    runs.append(mbp.mbp_decode_multi(args, 60, want_synd=True))
+    torch.cuda.synchronize()
+    converged = 0
+    for gi, g in enumerate(groups):
+        ref = orc.decode(g["H"], orc.bsc_llr(g["y"], g["n"], g["e"]), orc.syndrome(g["H"], g["x"]), 60, threads=8,
+                         want_synd=True)
+        conv = ref["success"].astype(bool)
+        converged += int(conv.sum())
+        for o in runs:
+            xh = o[gi]["x_hat_bits"].cpu().numpy().view(np.uint32)
+            ok = o[gi]["success"].cpu().numpy().astype(bool)
+            assert np.array_equal(ok[conv], ref["success"][conv]), pick[gi]
+            assert np.array_equal(xh[conv], ref["x_hat_bits"][conv]), pick[gi]
+            if "synd_ok" in o[gi]:
+                assert np.array_equal(o[gi]["synd_ok"].cpu().numpy()[conv], ref["synd_ok"][conv])
+            for l, zl in enumerate(orc.syndrome(g["H"], xh[ok])):
+                assert np.array_equal(zl, orc.syndrome(g["H"], g["x"][ok])[l])
+        it = runs[0][gi]["iters"].cpu().numpy()
+        print(pick[gi], "oracle iterations", ref["iters"].tolist(), "GPU", it.tolist())
+    assert converged >= 20
+
+
+@pytest.mark.slow
+def test_uneven_weakest_group_failures_are_the_oracles(mbp):
+    """The n = 2^14, rate-0.8, u = 2 group of the 4096-frame uneven workload (its QBERs reach 4%, near this
+    short code's decoding threshold): all of its frames through the grouped decode and the FP64 oracle. Bits
+    and flags agree where the oracle converges, and every frame the GPU fails to decode fails in the oracle
+    too (a frame that runs to max_iter is the code's failure, not the kernels')."""
+    sp = next(s for s in mi.uneven_batch(4096, 4) if (s["n"], s["rate"], s["u"]) == (16384, 0.8, 2))
+    H = mi.make_codes(sp["n"], sp["m"], sp["dist"], sp["u"], sp["cfg_seed"])
+    x, y, e = mi.bsc_frames(sp["n"], sp["frames"], sp["qber"], seed=sp["cfg_seed"])
+    codes = mbp.mbp_create_codes(H)
+    arg = dict(codes=codes, y_bits=dev(i32(y)), qber=dev(e), z_bits=mbp.mbp_syndrome(codes, dev(i32(x))))
+    o = mbp.mbp_decode_multi([arg], 60)[0]
+    torch.cuda.synchronize()
+    ref = orc.decode(H, orc.bsc_llr(y, sp["n"], e), orc.syndrome(H, x), 60, threads=8)
+    conv = ref["success"].astype(bool)
+    ok = o["success"].cpu().numpy().astype(bool)
+    xh = o["x_hat_bits"].cpu().numpy().view(np.uint32)
+    assert np.array_equal(ok[conv], ref["success"][conv]) and np.array_equal(xh[conv], ref["x_hat_bits"][conv])
+    assert not np.any(~ok & conv), "a frame the oracle decodes failed on the GPU"
+    print(f"{sp['frames']} frames: GPU failures {int((~ok).sum())}, oracle failures {int((~conv).sum())}, "
+          f"QBER of the failures {e[~ok].round(4).tolist()}")

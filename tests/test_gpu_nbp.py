@@ -102,6 +102,24 @@ def test_gradient_matches_fp64_reference(mbp, seed):
     assert rel_err(ga, ra) <= 2e-3 and rel_err(gb, rb) <= 2e-3 and rel_err(gl, rl) <= 2e-3
 
 
+@pytest.mark.slow
+def test_gradient_matches_fp64_reference_config5(mbp):
+    """The normalised-BP size: n = 16384, rate 0.6, u = 2, 20 unrolled iterations, on 2 frames at QBER 3%:
+    the hand-written adjoint against the FP64 autograd gradient (relative 2e-3 in the norm, as above)."""
+    c = Case(mbp, 16384, 6554, 2, 4, 2, 0.03)
+    T = 20
+    a, b = params(T, 2, 3)
+    a32, b32 = a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(17)
+    G = rng.normal(size=(T, c.F, c.n)) / (c.F * c.n)
+    lv, ga, gb, gl = grads_gpu(mbp, c, a32, b32, G)
+    ref_lv = onbp.forward_np(c.H, c.LP, c.z_orc, a32, b32)
+    _, ra, rb, rl = onbp.gradient(c.H, c.LP, c.z_orc, a32, b32, G)
+    print(f"T={T}: max |dL| {np.max(np.abs(lv.cpu().numpy() - ref_lv)):.3g}; relative errors: alpha "
+          f"{rel_err(ga, ra):.2e}, beta {rel_err(gb, rb):.2e}, llr {rel_err(gl, rl):.2e}")
+    assert rel_err(ga, ra) <= 2e-3 and rel_err(gb, rb) <= 2e-3 and rel_err(gl, rl) <= 2e-3
+
+
 def test_gradient_matches_central_differences(mbp):
     """J = BCE of sigmoid(-L^T) against the true bits; central differences of the GPU forward, eps = 1e-3."""
     c = Case(mbp, 1000, 400, 2, 21, 32, 0.06)
