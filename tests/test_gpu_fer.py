@@ -86,7 +86,7 @@ def test_fer_against_qber_headline_code(mbp):
             if q == 0.02:
                 assert r["fer_upper95"] < 1e-3, r
     waterfall = None
-    for q in (0.05, 0.06, 0.07, 0.08, 0.09, 0.10, 0.11, 0.12):
+    for q in (0.05, 0.06, 0.065, 0.07, 0.08, 0.09, 0.10, 0.11, 0.12):
         r = run_point(mbp, H, codes, q, 2048, mbp.MSG_F32, seed=52)
         r["msg"] = "f32"
         rows.append(r)
