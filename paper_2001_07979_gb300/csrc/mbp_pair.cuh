@@ -475,8 +475,9 @@ __global__ void __launch_bounds__(256) vn_rows_pair_kernel(const DevCode c, int 
 
 // vn_rows4_kernel (check degrees within 4 values) for a tile pair: one bit
 // transpose per tile, the degree offsets from two ballots, each tile's four
-// magnitudes in registers.
-template <int D, int NB>
+// magnitudes in registers. EXACT: every node of the class has D edges (no
+// per-edge test, the node loop unrolled).
+template <int D, int NB, bool EXACT = false>
 __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int cls, float* __restrict__ lv,
                                                             const uint32_t* __restrict__ yt,
                                                             const float* __restrict__ ymag, uint32_t* __restrict__ xh,
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
   const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
   if ((t.a0 | t.a1) == 0) return;
   const bool h0 = t.a0 != 0, h1 = t.a1 != 0;
-  const int d = c.vclass_deg[cls], N = kLanes / d;
+  const int d = EXACT ? D : c.vclass_deg[cls], N = kLanes / d;
   const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;
   const int q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * N;
   if (q0 >= count) return;
@@ -515,7 +516,11 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
   const float ym1 = h1 ? __ldg(ymag + t.t1 * kLanes + lane) : 0.f;
   const uint32_t a0b = __float_as_uint(ma[0]), da = __float_as_uint(ma[1 % (1 << NB)]) - a0b;
   const uint32_t b0b = __float_as_uint(mb[0]), db = __float_as_uint(mb[1 % (1 << NB)]) - b0b;
-  for (int j = 0; j < cnt; ++j) {
+  // the two magnitudes' bit patterns differ in xa / xb (NB = 1): an edge's pattern is a0b ^ (mask & xa)
+  const uint32_t xa = __float_as_uint(ma[1 % (1 << NB)]) ^ a0b, xb = __float_as_uint(mb[1 % (1 << NB)]) ^ b0b;
+#pragma unroll(EXACT ? kLanes / D : 1)
+  for (int j = 0; j < (EXACT ? kLanes / D : cnt); ++j) {
+    if (EXACT && j >= cnt) break;
     const int v = __shfl_sync(kFull, mycol, j);
     const uint32_t yl0 = (__shfl_sync(kFull, my0, j) >> lane) & 1u, yl1 = (__shfl_sync(kFull, my1, j) >> lane) & 1u;
     float sum0 = yl0 ? -ym0 : ym0, sum1 = yl1 ? -ym1 : ym1;
@@ -524,11 +529,13 @@ __global__ void __launch_bounds__(256) vn_rows4_pair_kernel(const DevCode c, int
     const uint32_t r0 = b0 >> base, r1 = b1 >> base;
 #pragma unroll
     for (int k = 0; k < D; ++k)
-      if (k < d) {
-        if constexpr (NB == 1) {  // bit patterns by integer multiply-adds, as in vn_rows4_kernel
-          const uint32_t rb = (r0 >> k) & 1u;
-          sum0 += __uint_as_float(a0b + rb * da + ((sg0 >> k) & 1u) * 0x80000000u);
-          sum1 += __uint_as_float(b0b + rb * db + ((sg1 >> k) & 1u) * 0x80000000u);
+      if (EXACT || k < d) {
+        if constexpr (NB == 1) {
+          // edge k's degree bit and sign bits moved to bit 31 by constant shifts: the magnitude's pattern
+          // (a0b or a0b ^ xa, the same value as a0b + rb * da) with the sign bit set where the sign is negative
+          const uint32_t mk = uint32_t(int32_t(r0 << (31 - k)) >> 31);
+          sum0 += __uint_as_float((a0b ^ (mk & xa)) | ((sg0 << (31 - k)) & kSign));
+          sum1 += __uint_as_float((b0b ^ (mk & xb)) | ((sg1 << (31 - k)) & kSign));
         } else {
           const bool c0 = r0 & (1u << k), c1 = r1 & (1u << k);
           const float x0 = c1 ? (c0 ? ma[3] : ma[2]) : (c0 ? ma[1] : ma[0]);

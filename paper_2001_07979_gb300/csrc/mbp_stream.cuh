@@ -379,7 +379,11 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
                                            static_cast<const float*>(st.chan_mag), st.xh, st.active, st.n_tiles, \
                                            static_cast<const float*>(st.fmag), st.rsgn)
           if (c.max_row_deg - c.min_row_deg <= 1) {
-            if (d <= 4) MBP_VR2(vn_rows4_pair_kernel, 4, 1);
+            if (d == 4) MBP_VR2(vn_rows4_pair_kernel, 4, 1, true);
+            else if (d == 6) MBP_VR2(vn_rows4_pair_kernel, 6, 1, true);
+            else if (d == 8) MBP_VR2(vn_rows4_pair_kernel, 8, 1, true);
+            else if (d == 16) MBP_VR2(vn_rows4_pair_kernel, 16, 1, true);
+            else if (d <= 4) MBP_VR2(vn_rows4_pair_kernel, 4, 1);
             else if (d <= 8) MBP_VR2(vn_rows4_pair_kernel, 8, 1);
             else MBP_VR2(vn_rows4_pair_kernel, 16, 1);
           } else if (c.max_row_deg - c.min_row_deg <= 3) {
