@@ -258,6 +258,22 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
                         int32_t* iters, uint8_t* success, mbp_stream_t stream);
 
 /*
+ * mbp_decode_bsc_host without the final wait: the input copies, the decode and
+ * the output copies are queued on `stream` and the call returns (once the
+ * decode is queued, see MBP_SCHED_AUTO). The caller synchronises `stream` (or
+ * an event recorded on it) before reading x_hat_bits, iters and success, and
+ * before changing y_bits, qber or z_bits. The host buffers should be
+ * page-locked (cudaHostAlloc / cudaHostRegister): copies from or to pageable
+ * memory may wait for the stream. Calls on one stream with one workspace run in
+ * order; calls that may overlap need workspaces of their own. This lets a
+ * caller keep the GPU busy while it prepares the next batch: the copies of one
+ * batch can run beside the decode of another on a second stream.
+ */
+int mbp_decode_bsc_host_async(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                              const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                              int32_t* iters, uint8_t* success, mbp_stream_t stream);
+
+/*
  * Copy the check-to-variable messages of one frame, as left in the workspace
  * by the last decode with these opts, to c2v_out (device, [edges] in stacked
  * CSR order: H_1's edges row by row, then H_2's, ...; double for F64, float

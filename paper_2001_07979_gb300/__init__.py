@@ -104,6 +104,7 @@ def _load():
             "mbp_decode_batch": (I, [P, I, P, P, I, P, P, P, P, P]),
             "mbp_decode_bsc": (I, [P, I, P, P, P, I, P, P, P, P, P]),
             "mbp_decode_bsc_host": (I, [P, I, P, P, P, I, P, P, P, P, P]),
+            "mbp_decode_bsc_host_async": (I, [P, I, P, P, P, I, P, P, P, P, P]),
             "mbp_export_c2v": (I, [P, I, P, I, P, P]),
             "mbp_multi_workspace_size": (I, [P, I, P, P]),
             "mbp_decode_multi": (I, [P, I, I, P, P]),
@@ -336,8 +337,10 @@ def mbp_decode_bsc_host(codes: Codes, y_bits: np.ndarray, qber: np.ndarray, z_bi
                         msg_dtype: int = MSG_F32, l_max: float = 20.0, early_exit: bool = True,
                         workspace: torch.Tensor | None = None, out: dict | None = None, stream=None,
                         device=None, accumulate: int = ACC_AUTO, schedule: int = SCHED_AUTO,
-                        rule: int = RULE_SUM_PRODUCT, update: int = UPDATE_FLOODING) -> dict:
-    """Host-memory variant: inputs and outputs are numpy arrays (or pinned CPU tensors)."""
+                        rule: int = RULE_SUM_PRODUCT, update: int = UPDATE_FLOODING, sync: bool = True) -> dict:
+    """Host-memory variant: inputs and outputs are numpy arrays (or pinned CPU tensors). sync=False calls
+    mbp_decode_bsc_host_async: the call returns once everything is queued on the stream, and the outputs are
+    valid (and the inputs free to change) only after the stream has been synchronised."""
     y = y_bits if isinstance(y_bits, torch.Tensor) else np.ascontiguousarray(y_bits, dtype=np.uint32)
     q = qber if isinstance(qber, torch.Tensor) else np.ascontiguousarray(qber, dtype=np.float64)
     z = z_bits if isinstance(z_bits, torch.Tensor) else np.ascontiguousarray(z_bits, dtype=np.uint32)
@@ -351,9 +354,9 @@ def mbp_decode_bsc_host(codes: Codes, y_bits: np.ndarray, qber: np.ndarray, z_bi
                    success=np.zeros(F, np.uint8))
     o = _opts(msg_dtype, l_max, early_exit, False, True, workspace, accumulate=accumulate, schedule=schedule,
               rule=rule, update=update)
-    _check(_load().mbp_decode_bsc_host(codes.handle, F, _ptr(y), _ptr(q), _ptr(z), int(max_iter), ctypes.byref(o),
-                                       _ptr(out["x_hat_bits"]), _ptr(out["iters"]), _ptr(out["success"]),
-                                       _stream_ptr(stream)))
+    entry = _load().mbp_decode_bsc_host if sync else _load().mbp_decode_bsc_host_async
+    _check(entry(codes.handle, F, _ptr(y), _ptr(q), _ptr(z), int(max_iter), ctypes.byref(o), _ptr(out["x_hat_bits"]),
+                 _ptr(out["iters"]), _ptr(out["success"]), _stream_ptr(stream)))
     out["workspace"] = workspace
     return out
 

@@ -589,10 +589,13 @@ int mbp_decode_bsc(const mbp_codes* codes, int F, const uint32_t* y_bits, const 
                        stream);
 }
 
-int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
-                        const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
-                        int32_t* iters, uint8_t* success, mbp_stream_t stream) {
-  g_err.clear();
+}  // extern "C"
+
+// The host-memory decode: inputs copied into the workspace's staging buffers, the decode, the outputs copied
+// back; with sync, the call waits for the stream at the end.
+static int decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                           const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                           int32_t* iters, uint8_t* success, mbp_stream_t stream, bool sync) {
   int rc = common_decode_checks(codes, F, max_iter, opts);
   if (rc || F == 0) return rc;
   REQUIRE(opts->host_io == 1, "opts->host_io must be 1 for mbp_decode_bsc_host");
@@ -647,9 +650,25 @@ int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, c
   CK(cudaMemcpyAsync(x_hat_bits, st.io_xhat, size_t(F) * wn * 4, cudaMemcpyDeviceToHost, s), "copy x_hat to host");
   CK(cudaMemcpyAsync(iters, st.io_iters, size_t(F) * 4, cudaMemcpyDeviceToHost, s), "copy iters to host");
   CK(cudaMemcpyAsync(success, st.io_success, size_t(F), cudaMemcpyDeviceToHost, s), "copy success to host");
-  CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  if (sync) CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
 #undef CK
   return MBP_OK;
+}
+
+extern "C" {
+
+int mbp_decode_bsc_host(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                        const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                        int32_t* iters, uint8_t* success, mbp_stream_t stream) {
+  g_err.clear();
+  return decode_bsc_host(codes, F, y_bits, qber, z_bits, max_iter, opts, x_hat_bits, iters, success, stream, true);
+}
+
+int mbp_decode_bsc_host_async(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
+                              const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
+                              int32_t* iters, uint8_t* success, mbp_stream_t stream) {
+  g_err.clear();
+  return decode_bsc_host(codes, F, y_bits, qber, z_bits, max_iter, opts, x_hat_bits, iters, success, stream, false);
 }
 
 int mbp_decode_bsc_static(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,

@@ -335,6 +335,37 @@ def test_host_io_entry_matches_device_entry(mbp):
     assert np.array_equal(a["success"].cpu().numpy(), b["success"])
 
 
+@pytest.mark.parametrize("sched", ["auto", "streaming"])
+def test_host_io_async_entry_pipelined_on_two_streams(mbp, sched):
+    """mbp_decode_bsc_host_async from pinned host memory, six batches alternating over two streams (each with
+    its own workspace and output buffers), one synchronisation at the end: every batch equals the device-memory
+    decode of the same frames."""
+    sch = mbp.SCHED_AUTO if sched == "auto" else mbp.SCHED_STREAMING
+    w = Workload(4000, 1600, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 3, 6 * 21, 0.05)
+    codes = mbp.mbp_create_codes(w.H)
+    z = gpu_syndrome(mbp, codes, w.x)
+    zs = mbp.split_syndromes(codes, z, w.F)
+    lanes = [torch.cuda.Stream() for _ in range(2)]
+    ws = [torch.empty(mbp.mbp_decode_workspace_size(codes, 21, host_io=True, schedule=sch), dtype=torch.uint8,
+                      device="cuda") for _ in lanes]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    outs = []
+    for b in range(6):
+        sl = slice(21 * b, 21 * (b + 1))
+        zb = pin(mbp.join_syndromes([p[sl] for p in zs]).cpu())
+        out = dict(x_hat_bits=pin(np.zeros((21, (w.n + 31) // 32), np.int32)), iters=pin(np.zeros(21, np.int32)),
+                   success=pin(np.zeros(21, np.uint8)))
+        mbp.mbp_decode_bsc_host(codes, pin(u32_to_i32(w.y[sl])), pin(w.e[sl]), zb, 30, workspace=ws[b % 2], out=out,
+                                stream=lanes[b % 2], schedule=sch, sync=False)
+        outs.append((sl, zb, out))
+    torch.cuda.synchronize()
+    for sl, zb, out in outs:
+        ref = mbp.mbp_decode_bsc(codes, dev(u32_to_i32(w.y[sl])), dev(w.e[sl]), zb.cuda(), 30, schedule=sch)
+        assert np.array_equal(host_u32(ref["x_hat_bits"]), out["x_hat_bits"].numpy().view(np.uint32))
+        assert np.array_equal(ref["iters"].cpu().numpy(), out["iters"].numpy())
+        assert np.array_equal(ref["success"].cpu().numpy(), out["success"].numpy())
+
+
 def test_invalid_arguments_return_errors(mbp):
     w = Workload(512, 200, {3: 1.0}, 2, 3, 8, 0.05)
     codes = mbp.mbp_create_codes(w.H)
