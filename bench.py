@@ -8,9 +8,9 @@ variable degrees {2: 30%, 3: 40%, 8: 30%}, QBER 2%, 1024 frames, at most 60
 flooding iterations, FP32 messages. Frames are synthetic (seeded), the codes
 are built by the seeded PEG generator. The timed steps cycle through 8 distinct
 batches, so the frame error rate is counted over 8192 distinct frames, and
-alternate over two CUDA streams (a workspace each), so that two independent
-batches are in flight as in a server; the one-stream figure is reported beside
-it.
+alternate over four CUDA streams (a workspace each), so that independent
+batches are in flight together as in a server; the one-stream figure is
+reported beside it.
 
 The metric is corrected sifted key per second: sum over frames of n divided by
 the decode time, all frames counted (the frame error rate is reported beside
@@ -62,7 +62,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--frames", type=int, default=FRAMES)
     p.add_argument("--batches", type=int, default=8, help="distinct frame batches cycled through the timed steps")
-    p.add_argument("--streams", type=int, default=2, help="streams the steps' decodes alternate over")
+    p.add_argument("--streams", type=int, default=4, help="streams the steps' decodes alternate over")
     p.add_argument("--no-extras", action="store_true", help="skip the QBER-4%% and FP16/BF16 side measurements")
     p.add_argument("--cpu-sample", type=int, default=256, help="frames in the oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
