@@ -125,12 +125,33 @@ __device__ __forceinline__ PairTiles pair_tiles(int q, int n_tiles, const uint32
   return p;
 }
 
+// Rows of more than 16 edges keep only the prefix folds before even edges (the
+// one before an odd edge k is formed again from the one before k - 1 and delta
+// k - 1: the same operation on the same values), so that the two tiles' rows
+// fit three blocks per SM.
+template <int D>
+constexpr bool kHalfPrefix = D > 16;
+template <int D>
+constexpr int kPrefixLen = kHalfPrefix<D> ? (D + 1) / 2 : D;
+
+// The (+) fold of edges 0 .. k - 1; v[k - 1] holds delta k - 1 (its sign bit
+// carries the V2C's sign).
+template <int D>
+__device__ __forceinline__ float pair_prefix(const float (&pre)[kPrefixLen<D>], const float (&v)[D], int k) {
+  if constexpr (kHalfPrefix<D>) {
+    if (k & 1) return Arith<float>::oplus(pre[k >> 1], fabsf(v[k - 1]));
+    return pre[k >> 1];
+  } else {
+    return pre[k];
+  }
+}
+
 // The prefix pass of eq. (6) for one frame: the row's sign parity into par,
-// each V2C replaced by its delta carrying the V2C's sign bit, pre[k] the (+)
-// fold of edges 0 .. k - 1 (padding edges fold as 0).
+// each V2C replaced by its delta carrying the V2C's sign bit, pre the (+)
+// folds of edges 0 .. k - 1 (padding edges fold as 0).
 template <int D, bool CHECKED>
-__device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre)[D], uint32_t& par, float l_max,
-                                             float d_lmax) {
+__device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre)[kPrefixLen<D>], uint32_t& par,
+                                             float l_max, float d_lmax) {
   using A = Arith<float>;
   using B = Bits<float>;
   float P = 0.f;
@@ -141,7 +162,7 @@ __device__ __forceinline__ void cn_pair_fold(int deg, float (&v)[D], float (&pre
     float d = A::clipped_delta(v[k], l_max, d_lmax);
     if constexpr (CHECKED) d = k < deg ? d : 0.f;
     v[k] = B::with_sign(d, x & kSign);
-    pre[k] = P;
+    if (!kHalfPrefix<D> || (k & 1) == 0) pre[kHalfPrefix<D> ? k >> 1 : k] = P;
     P = A::oplus(P, d);
   }
 }
@@ -198,14 +219,14 @@ __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ col
   }
   if (!s0 && !s1) return;
   // tile 0, then tile 1, sharing the prefix array; tile 0's outputs replace its deltas in v0
-  float pre[D];
+  float pre[kPrefixLen<D>];
   cn_pair_fold<D, CHECKED>(deg, v0, pre, par0, l_max, d_lmax);
   float q = 0.f;
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
     const float d = v0[k];
     if (!CHECKED || k < deg)
-      v0[k] = B::copy_sign(A::clipped_mag(A::oplus(pre[k], q), l_max), par0 ^ B::sign_word(d));
+      v0[k] = B::copy_sign(A::clipped_mag(A::oplus(pair_prefix<D>(pre, v0, k), q), l_max), par0 ^ B::sign_word(d));
     q = A::oplus(q, fabsf(d));
   }
   cn_pair_fold<D, CHECKED>(deg, v1, pre, par1, l_max, d_lmax);
@@ -213,7 +234,7 @@ __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ col
 #pragma unroll
   for (int k = D - 1; k >= 0; --k) {
     if (!CHECKED || k < deg) {
-      const float m1 = A::clipped_mag(A::oplus(pre[k], q), l_max);
+      const float m1 = A::clipped_mag(A::oplus(pair_prefix<D>(pre, v1, k), q), l_max);
       st_pair<S>(msg + k * Pair<S>::kSlot, v0[k], B::copy_sign(m1, par1 ^ B::sign_word(v1[k])), s0, s1);
     }
     q = A::oplus(q, fabsf(v1[k]));
@@ -253,7 +274,7 @@ __device__ __forceinline__ void cn_pair_row_signs(int deg, const int* __restrict
 
 // Resident blocks of 256 threads per SM for the pair check kernel: two frames
 // per lane double the row's registers.
-constexpr int cn_pair_min_blocks(int dmax) { return dmax <= 14 ? 4 : (dmax <= 16 ? 3 : 2); }
+constexpr int cn_pair_min_blocks(int dmax) { return dmax <= 14 ? 4 : 3; }
 
 // One warp per (tile pair, check row): 8 rows per block, pair = blockIdx.y,
 // rows p0 .. p1 - 1. RIN: iteration 2 after a row-form iteration 1 (fmag, rsgn;
@@ -344,7 +365,7 @@ __global__ void __launch_bounds__(256) vn_class_pair_kernel(const DevCode c, int
                                                             const uint32_t* __restrict__ yt,
                                                             const float* __restrict__ ymag, uint32_t* __restrict__ xh,
                                                             const uint32_t* __restrict__ active, int n_tiles) {
-  static_assert(D <= 16, "short classes only");
+  static_assert(D <= 32, "classes of up to 32 edges");
   const PairTiles t = pair_tiles(blockIdx.y, n_tiles, active);
   if ((t.a0 | t.a1) == 0) return;
   const int first = c.vclass_first[cls], count = c.vclass_first[cls + 1] - first;

@@ -356,9 +356,9 @@ __global__ void __launch_bounds__(256) vn_rows4_kernel(const DevCode c, int cls,
 
 // Whether iteration 1 of a flooding sum-product decode keeps its messages in row
 // form (DevState::fmag): BSC inputs (one channel magnitude per frame) and every
-// variable-node class of at most 16 edges.
+// variable-node class of at most 32 edges.
 inline bool rows_ok(const DevCode& c, const DevState& st) {
-  return st.yt && st.fmag && c.vrow && c.n_vclass > 0 && c.vclass_deg[c.n_vclass - 1] <= 16 &&
+  return st.yt && st.fmag && c.vrow && c.n_vclass > 0 && c.vclass_deg[c.n_vclass - 1] <= 32 &&
          c.max_row_deg <= 32;
 }
 
@@ -369,7 +369,7 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
   if (c.n_vclass > 0) {
     for (int k = 0; k < c.n_vclass; ++k) {
       const int count = c.vclass_first[k + 1] - c.vclass_first[k], d = c.vclass_deg[k];
-      if (rows) {  // classes of up to 16 edges (rows_ok), 32 / d nodes per warp
+      if (rows) {  // classes of up to 32 edges (rows_ok), 32 / d nodes per warp
         const int per_warp = kLanes / d;
         const unsigned blocks = blocks_for(count, 8 * per_warp);
         if constexpr (kPairKernels<M, S>) {
@@ -383,17 +383,21 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
             else if (d == 6) MBP_VR2(vn_rows4_pair_kernel, 6, 1, true);
             else if (d == 8) MBP_VR2(vn_rows4_pair_kernel, 8, 1, true);
             else if (d == 16) MBP_VR2(vn_rows4_pair_kernel, 16, 1, true);
+            else if (d == 24) MBP_VR2(vn_rows4_pair_kernel, 24, 1, true);
             else if (d <= 4) MBP_VR2(vn_rows4_pair_kernel, 4, 1);
             else if (d <= 8) MBP_VR2(vn_rows4_pair_kernel, 8, 1);
-            else MBP_VR2(vn_rows4_pair_kernel, 16, 1);
+            else if (d <= 16) MBP_VR2(vn_rows4_pair_kernel, 16, 1);
+            else MBP_VR2(vn_rows4_pair_kernel, 32, 1);
           } else if (c.max_row_deg - c.min_row_deg <= 3) {
             if (d <= 4) MBP_VR2(vn_rows4_pair_kernel, 4, 2);
             else if (d <= 8) MBP_VR2(vn_rows4_pair_kernel, 8, 2);
-            else MBP_VR2(vn_rows4_pair_kernel, 16, 2);
+            else if (d <= 16) MBP_VR2(vn_rows4_pair_kernel, 16, 2);
+            else MBP_VR2(vn_rows4_pair_kernel, 32, 2);
           } else {
             if (d <= 4) MBP_VR2(vn_rows_pair_kernel, 4);
             else if (d <= 8) MBP_VR2(vn_rows_pair_kernel, 8);
-            else MBP_VR2(vn_rows_pair_kernel, 16);
+            else if (d <= 16) MBP_VR2(vn_rows_pair_kernel, 16);
+            else MBP_VR2(vn_rows_pair_kernel, 32);
           }
 #undef MBP_VR2
         } else {
@@ -404,15 +408,18 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
           if (c.max_row_deg - c.min_row_deg <= 1) {
             if (d <= 4) MBP_VR(vn_rows4_kernel, 4, 1);
             else if (d <= 8) MBP_VR(vn_rows4_kernel, 8, 1);
-            else MBP_VR(vn_rows4_kernel, 16, 1);
+            else if (d <= 16) MBP_VR(vn_rows4_kernel, 16, 1);
+            else MBP_VR(vn_rows4_kernel, 32, 1);
           } else if (c.max_row_deg - c.min_row_deg <= 3) {
             if (d <= 4) MBP_VR(vn_rows4_kernel, 4, 2);
             else if (d <= 8) MBP_VR(vn_rows4_kernel, 8, 2);
-            else MBP_VR(vn_rows4_kernel, 16, 2);
+            else if (d <= 16) MBP_VR(vn_rows4_kernel, 16, 2);
+            else MBP_VR(vn_rows4_kernel, 32, 2);
           } else {
             if (d <= 4) MBP_VR(vn_rows_kernel, 4);
             else if (d <= 8) MBP_VR(vn_rows_kernel, 8);
-            else MBP_VR(vn_rows_kernel, 16);
+            else if (d <= 16) MBP_VR(vn_rows_kernel, 16);
+            else MBP_VR(vn_rows_kernel, 32);
           }
 #undef MBP_VR
         }
@@ -431,6 +438,8 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
         if (d <= 6) { MBP_VN2(6, 2); continue; }
         if (d <= 8) { MBP_VN2(8, 2); continue; }
         if (d <= 16) { MBP_VN2(16, 1); continue; }
+        if (d <= 24) { MBP_VN2(24, 1); continue; }
+        if (d <= 32) { MBP_VN2(32, 1); continue; }
 #undef MBP_VN2
       }
 #define MBP_VN(D, N)                                                                                        \
