@@ -43,3 +43,16 @@ def test_traffic_only_for_matching_digest_and_type(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "0" * 16)
     assert bench.kernel_traffic([3], 1, "k.txt", "f32", rows=True) is None
     assert os.path.isdir(real_root)
+
+
+def test_fer_upper_bound_is_clopper_pearson():
+    # no error in n frames: 1 - 0.05^(1/n), about 3/n (the rule of three)
+    assert bench.fer_upper95(0, 8192) == 1.0 - 0.05 ** (1.0 / 8192)
+    assert abs(bench.fer_upper95(0, 8192) * 8192 - 3.0) < 0.01
+    # k errors: the upper end of the one-sided 95% interval, where P(X <= k) = 0.05 for X ~ Bin(n, p)
+    import math
+    for k, n in ((1, 100), (5, 2048), (24, 2048)):
+        p = bench.fer_upper95(k, n)
+        cdf = sum(math.comb(n, i) * p ** i * (1 - p) ** (n - i) for i in range(k + 1))
+        assert abs(cdf - 0.05) < 1e-6, (k, n, cdf)
+    assert bench.fer_upper95(3, 3) == 1.0
