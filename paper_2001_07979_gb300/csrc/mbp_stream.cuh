@@ -488,43 +488,60 @@ __global__ void __launch_bounds__(256) finalize_kernel(const DevCode c, const in
 // consecutive check rows (in position order, so one matrix except where the
 // matrices meet) for 32 tiles, lane = tile (tiles 32 y .. 32 y + 31, y =
 // blockIdx.y): every edge's words for those tiles are one coalesced line. The
-// failing lanes of each tile are ORed over the warp's rows and then into
-// fail[tile][l], once per matrix met.
+// failing lanes of each tile are ORed over the warp's rows, then over the
+// block's warps in shared memory, and each block ORs its result into
+// fail[tile][l] only where it sets bits that are not set yet (in the iterations
+// where most frames still fail, the first blocks set them and the others skip
+// the global atomic, which would otherwise queue thousands of times on the same
+// few words).
 template <int DMAX>
 __global__ void __launch_bounds__(256) syn_kernel(const DevCode c, int n_tiles, const uint32_t* __restrict__ xh,
                                                   const uint32_t* __restrict__ ztt,
                                                   const uint32_t* __restrict__ active, uint32_t* __restrict__ fail) {
+  __shared__ uint32_t s_fail[kMaxU][kLanes];
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.y * kLanes + lane;
   const bool tv = tile < n_tiles;
   const uint32_t act = tv ? active[tile] : 0u;
-  if (__ballot_sync(kFull, act != 0) == 0) return;
+  if (__syncthreads_or(act != 0) == 0) return;  // every tile of the block has finished
+  for (int i = threadIdx.x; i < c.u * kLanes; i += blockDim.x) s_fail[i / kLanes][i % kLanes] = 0u;
+  __syncthreads();
   const int r0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * kSynRows;
-  if (r0 >= c.m_tot) return;
-  uint32_t acc = 0;
-  int lcur = c.row_mat[r0];
+  if (r0 < c.m_tot) {
+    uint32_t acc = 0;
+    int lcur = c.row_mat[r0];
 #pragma unroll
-  for (int i = 0; i < kSynRows; ++i) {
-    const int r = r0 + i;
-    if (r >= c.m_tot) break;
-    const int l = c.row_mat[r];
-    if (l != lcur) {  // warp-uniform
-      if (acc) atomicOr(&fail[tile * c.u + lcur], acc);
-      acc = 0;
-      lcur = l;
+    for (int i = 0; i < kSynRows; ++i) {
+      const int r = r0 + i;
+      if (r >= c.m_tot) break;
+      const int l = c.row_mat[r];
+      if (l != lcur) {  // warp-uniform
+        if (acc) atomicOr(&s_fail[lcur][lane], acc);
+        acc = 0;
+        lcur = l;
+      }
+      const int base = c.slice_base[r];
+      const int deg = c.slice_base[r + 1] - base;
+      int col[DMAX];
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(c.slot_col + base + k) : -1;
+      uint32_t w = tv ? __ldg(ztt + int64_t(r) * n_tiles + tile) : 0u;
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k)
+        if (col[k] >= 0 && tv) w ^= __ldg(xh + int64_t(col[k]) * n_tiles + tile);
+      acc |= w & act;
     }
-    const int base = c.slice_base[r];
-    const int deg = c.slice_base[r + 1] - base;
-    int col[DMAX];
-#pragma unroll
-    for (int k = 0; k < DMAX; ++k) col[k] = k < deg ? __ldg(c.slot_col + base + k) : -1;
-    uint32_t w = tv ? __ldg(ztt + int64_t(r) * n_tiles + tile) : 0u;
-#pragma unroll
-    for (int k = 0; k < DMAX; ++k)
-      if (col[k] >= 0 && tv) w ^= __ldg(xh + int64_t(col[k]) * n_tiles + tile);
-    acc |= w & act;
+    if (acc) atomicOr(&s_fail[lcur][lane], acc);
   }
-  if (acc) atomicOr(&fail[tile * c.u + lcur], acc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < c.u * kLanes; i += blockDim.x) {
+    const uint32_t v = s_fail[i / kLanes][i % kLanes];
+    const int t = blockIdx.y * kLanes + i % kLanes;
+    if (v && t < n_tiles) {
+      uint32_t* f = fail + int64_t(t) * c.u + i / kLanes;
+      if ((__ldcg(f) & v) != v) atomicOr(f, v);
+    }
+  }
 }
 
 template <int DMAX>
