@@ -475,6 +475,9 @@ def run_gb300(args):
     b_path = sum(per_batch[s % B][1] for s in range(args.steps)) / args.steps
     iters_steps = np.concatenate([iters_b[s % B] for s in range(args.steps)])
     peak, peak_src = load_peaks()
+    # the floor of one frame-iteration, B_it = 2 s E + 12 n (every message read and written once, the posterior
+    # read, written and gathered once), times the frame-iterations the timed steps ran
+    b_it = (2 * msg_bytes * e_tot + 12 * N) * float(iters_steps.sum()) / args.steps
     dominant = "persistent" if prof.get("persistent", (0, 0.0))[0] > 0 else "check"
     launches = int(sum(v[0] for v in prof.values()))
     path_gbs = b_path / (ms / 1e3) / 1e9
@@ -558,7 +561,10 @@ def run_gb300(args):
                          "path_bytes_rule": ("per frame: 4n (iteration 1, row form), 2*s*E+8n (iteration 2), "
                                              "3*s*E+8n later" if rows else
                                              "per frame: 2*s*E+8n (iteration 1), 3*s*E+8n later"),
-                         "row_form": rows},
+                         "row_form": rows,
+                         "b_it_gbs": b_it / (ms / 1e3) / 1e9, "b_it_frac": b_it / (ms / 1e3) / 1e9 / peak,
+                         "b_it_rule": "B_it = 2*s*E + 12n per executed frame-iteration (the method's floor), "
+                                      "times the frame-iterations of a step, over the step time"},
             "kernel_ms": {k: v[1] / args.steps for k, v in prof.items()},
             "kernel_ms_source": "a second pass of the same steps with a CUDA event pair around every kernel launch",
             "gpu_launches": launches,
