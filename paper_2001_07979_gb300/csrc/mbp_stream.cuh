@@ -121,41 +121,74 @@ __global__ void __launch_bounds__(256) cn_first_kernel(const DevCode c, int p0, 
 // (node-major: one coalesced line per edge for 32 tiles) wherever the frame's
 // channel magnitude is positive; the bits of other frames come from yt. A warp
 // takes kSynRows rows, lane = tile, and writes the words row-major; the kernel
-// sets the row-form flag counters[2].
+// sets the row-form flag counters[2]. The row's parity before the correction to
+// Bob's bits is that of the hard decision of iteration 0, so with fail != NULL
+// the kernel is also the stopping test before iteration 1: as in syn_kernel, the
+// failing lanes are ORed per block and then into fail[tile][l].
 template <int DMAX>
 __global__ void __launch_bounds__(256) first_rows_kernel(const DevCode c, int n_tiles, const uint32_t* __restrict__ xh,
                                                          const uint32_t* __restrict__ ztt,
                                                          const uint32_t* __restrict__ yt,
                                                          const uint32_t* __restrict__ ppos,
                                                          const uint32_t* __restrict__ active,
-                                                         uint32_t* __restrict__ rsgn, int32_t* __restrict__ counters) {
+                                                         uint32_t* __restrict__ rsgn, int32_t* __restrict__ counters,
+                                                         uint32_t* __restrict__ fail) {
+  __shared__ uint32_t s_fail[kMaxU][kLanes];
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) counters[2] = 1;
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.y * kLanes + lane;
   const bool tv = tile < n_tiles;
   const uint32_t act = tv ? active[tile] : 0u;
-  if (__ballot_sync(kFull, act != 0) == 0) return;
+  if (__syncthreads_or(act != 0) == 0) return;  // every tile of the block has finished
+  if (fail) {
+    for (int i = threadIdx.x; i < c.u * kLanes; i += blockDim.x) s_fail[i / kLanes][i % kLanes] = 0u;
+    __syncthreads();
+  }
   const int r0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * kSynRows;
-  if (r0 >= c.m_tot) return;
-  const uint32_t pp = tv ? ppos[tile] : kFull;
-  const uint32_t* y = yt + int64_t(tv ? tile : 0) * c.n;
+  if (r0 < c.m_tot) {
+    const uint32_t pp = tv ? ppos[tile] : kFull;
+    const uint32_t* y = yt + int64_t(tv ? tile : 0) * c.n;
+    uint32_t acc = 0;
+    int lcur = c.row_mat[r0];
 #pragma unroll
-  for (int i = 0; i < kSynRows; ++i) {
-    const int r = r0 + i;
-    if (r < c.m_tot) {
-      const int base = c.slice_base[r];
-      const int deg = c.slice_base[r + 1] - base;
-      uint32_t x = tv ? __ldg(ztt + int64_t(r) * n_tiles + tile) : 0u;
+    for (int i = 0; i < kSynRows; ++i) {
+      const int r = r0 + i;
+      if (r < c.m_tot) {
+        const int base = c.slice_base[r];
+        const int deg = c.slice_base[r + 1] - base;
+        uint32_t x = tv ? __ldg(ztt + int64_t(r) * n_tiles + tile) : 0u;
+        uint32_t yb = 0u;
 #pragma unroll
-      for (int k = 0; k < DMAX; ++k)
-        if (k < deg) {
-          const int col = __ldg(c.slot_col + base + k);
-          if (tv) {
-            x ^= __ldg(xh + int64_t(col) * n_tiles + tile);
-            if (pp != kFull) x ^= __ldg(y + col) & ~pp;
+        for (int k = 0; k < DMAX; ++k)
+          if (k < deg) {
+            const int col = __ldg(c.slot_col + base + k);
+            if (tv) {
+              x ^= __ldg(xh + int64_t(col) * n_tiles + tile);
+              if (pp != kFull) yb ^= __ldg(y + col) & ~pp;
+            }
           }
+        if (fail) {  // the stopping test before iteration 1: the row's failing lanes of the hard decision x_0
+          const int l = c.row_mat[r];
+          if (l != lcur) {  // warp-uniform
+            if (acc) atomicOr(&s_fail[lcur][lane], acc);
+            acc = 0;
+            lcur = l;
+          }
+          acc |= x & act;
         }
-      if (tv) rsgn[int64_t(r) * n_tiles + tile] = x;
+        if (tv) rsgn[int64_t(r) * n_tiles + tile] = x ^ yb;
+      }
+    }
+    if (fail && acc) atomicOr(&s_fail[lcur][lane], acc);
+  }
+  if (!fail) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < c.u * kLanes; i += blockDim.x) {
+    const uint32_t v = s_fail[i / kLanes][i % kLanes];
+    const int t = blockIdx.y * kLanes + i % kLanes;
+    if (v && t < n_tiles) {
+      uint32_t* f = fail + int64_t(t) * c.u + i / kLanes;
+      if ((__ldcg(f) & v) != v) atomicOr(f, v);
     }
   }
 }
@@ -568,10 +601,38 @@ __global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, in
     atomicAdd(&counters[0], 1);
 }
 
+// The rows' sign words of iteration 1 in row form; with fail, also the stopping test before iteration 1.
+template <int DMAX>
+void launch_first_rows(const DevCode& c, const DevState& st, const uint32_t* yt, uint32_t* fail, cudaStream_t s) {
+  first_rows_kernel<DMAX><<<dim3(blocks_for(c.m_tot, 8 * kSynRows), unsigned((st.n_tiles + kLanes - 1) / kLanes)),
+                            256, 0, s>>>(c, st.n_tiles, st.xh, st.ztt, yt, st.ppos, st.active, st.rsgn, st.counters,
+                                         fail);
+}
+
+// The same unroll bounds as the check kernels of FP32 arithmetic (rows of at most 32 edges: rows_ok).
+inline void launch_first_rows_any(const DevCode& c, const DevState& st, uint32_t* fail, cudaStream_t s) {
+  const int d = c.max_row_deg;
+#define MBP_FR(D) launch_first_rows<D>(c, st, st.yt, fail, s)
+  if (d <= 4) MBP_FR(4);
+  else if (d <= 6) MBP_FR(6);
+  else if (d <= 8) MBP_FR(8);
+  else if (d <= 10) MBP_FR(10);
+  else if (d <= 12) MBP_FR(12);
+  else if (d <= 14) MBP_FR(14);
+  else if (d <= 16) MBP_FR(16);
+  else if (d <= 18) MBP_FR(18);
+  else if (d <= 20) MBP_FR(20);
+  else if (d <= 22) MBP_FR(22);
+  else if (d <= 24) MBP_FR(24);
+  else MBP_FR(32);
+#undef MBP_FR
+}
+
 // Rows p0 .. p1 - 1 of every tile that is still decoding, from the posterior (or L_P) lsrc, or from the sign
 // words yt in the first iteration of BSC inputs.
-// rows: 1 = iteration 1 writes its messages in row form, 2 = iteration 2 reads
-// the previous messages in row form, 0 = per edge.
+// rows: 1 = iteration 1 writes its messages in row form, 3 = the same with the
+// rows' sign words already formed (by the stopping test before iteration 1),
+// 2 = iteration 2 reads the previous messages in row form, 0 = per edge.
 struct CnLaunch {
   int p0, p1, first_iter;
   const void* lsrc;
@@ -584,10 +645,8 @@ void launch_cn(const DevCode& c, const DevState& st, const CnLaunch& q, double l
                cudaStream_t s) {
   const dim3 grid(blocks_for(q.p1 - q.p0, 8), st.n_tiles);
   if constexpr (!FIXED && DMAX <= 32) {
-    if (q.rows == 1) {  // iteration 1 in row form: the rows' sign words and the magnitude table
-      first_rows_kernel<DMAX><<<dim3(blocks_for(c.m_tot, 8 * kSynRows), unsigned((st.n_tiles + kLanes - 1) / kLanes)),
-                                256, 0, s>>>(c, st.n_tiles, st.xh, st.ztt, q.yt, st.ppos, st.active, st.rsgn,
-                                             st.counters);
+    if (q.rows == 1 || q.rows == 3) {  // iteration 1 in row form: the rows' sign words and the magnitude table
+      if (q.rows == 1) launch_first_rows<DMAX>(c, st, q.yt, nullptr, s);
       const int cells = st.n_tiles * c.max_row_deg * kLanes;
       first_mag_kernel<M, S><<<blocks_for(cells, 256), 256, 0, s>>>(st.n_tiles, c.max_row_deg,
                                                                    static_cast<const M*>(st.chan_mag), M(l_max),
@@ -688,12 +747,14 @@ void launch_cn_any(const DevCode& c, const DevState& st, const CnLaunch& q, doub
 // kStopTestOnly: the stopping test before iteration 1.
 template <typename M, typename S>
 cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s) {
-  if (iter == kStopTestOnly) {
-    launch_syn_any(c, st, s);
+  const bool rows = rows_ok(c, st);
+  if (iter == kStopTestOnly) {  // with the row form, the sign words of iteration 1 and the test together
+    if (rows) launch_first_rows_any(c, st, st.fail, s);
+    else launch_syn_any(c, st, s);
     return cudaGetLastError();
   }
-  const bool rows = rows_ok(c, st);
-  const CnLaunch q{0, c.m_tot, iter == 1, iter == 1 ? st.lp : st.lv, st.yt, rows ? (iter == 1 || iter == 2 ? iter : 0) : 0};
+  // iteration 1 in row form follows the stopping test, which formed the rows' sign words (rows = 3)
+  const CnLaunch q{0, c.m_tot, iter == 1, iter == 1 ? st.lp : st.lv, st.yt, rows ? (iter == 1 ? 3 : iter == 2 ? 2 : 0) : 0};
   const int fam = q.rows ? MBP_KERNEL_CHECK_ROWS : MBP_KERNEL_CHECK;
   prof_begin(fam, s);
   launch_cn_any<M, S, false>(c, st, q, l_max, 0.f, MBP_RULE_SUM_PRODUCT, s);
@@ -721,11 +782,14 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
   const int F = st.F, NT = st.n_tiles;
   const dim3 node_grid(blocks_for(c.n, 8), NT);
   int32_t host_ctr[1];
-  auto stop_check = [&](int t, int* left) -> int {
-    prof_begin(MBP_KERNEL_SYNDROME, s);
-    launch_syn_any(c, st, s);
-    CKL("syn_kernel");
-    prof_end(MBP_KERNEL_SYNDROME, s, 1);
+  // tested: the syndrome test already ran (folded into the first row-form kernel before iteration 1)
+  auto stop_check = [&](int t, int* left, bool tested = false) -> int {
+    if (!tested) {
+      prof_begin(MBP_KERNEL_SYNDROME, s);
+      launch_syn_any(c, st, s);
+      CKL("syn_kernel");
+      prof_end(MBP_KERNEL_SYNDROME, s, 1);
+    }
     CK(cudaMemsetAsync(st.counters, 0, sizeof(int32_t), s), "clear counter");
     prof_begin(MBP_KERNEL_RETIRE, s);
     update_kernel<<<blocks_for(NT, 128), 128, 0, s>>>(F, NT, c.u, t, a.max_iter, a.early_exit, st.active, st.fail,
@@ -739,7 +803,16 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
   };
   int left = NT;
   int rc;
-  if (a.early_exit || a.max_iter == 0) {
+  const bool serial0 = a.update == MBP_UPDATE_MATRIX_SERIAL && c.u > 1;
+  // iteration 1 in row form: its rows' sign words come with the stopping test before it (rows0)
+  const bool rows0 = !fixed && !serial0 && a.rule == MBP_RULE_SUM_PRODUCT && rows_ok(c, st) && a.max_iter > 0;
+  if (rows0) {
+    prof_begin(MBP_KERNEL_CHECK_ROWS, s);
+    launch_first_rows_any(c, st, a.early_exit ? st.fail : nullptr, s);
+    CKL("first_rows_kernel");
+    prof_end(MBP_KERNEL_CHECK_ROWS, s, 1);
+    if (a.early_exit && (rc = stop_check(0, &left, true))) return rc;
+  } else if (a.early_exit || a.max_iter == 0) {
     if ((rc = stop_check(0, &left))) return rc;
   }
   auto variable = [&](bool rows) -> int {
@@ -782,7 +855,7 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
         if ((rc = variable(false))) return rc;
       }
     } else {
-      const CnLaunch q{0, c.m_tot, t == 1, t == 1 ? st.lp : st.lv, st.yt, rows ? (t <= 2 ? t : 0) : 0};
+      const CnLaunch q{0, c.m_tot, t == 1, t == 1 ? st.lp : st.lv, st.yt, rows ? (t == 1 ? 3 : t == 2 ? 2 : 0) : 0};
       if ((rc = check(q))) return rc;
       if ((rc = variable(rows && t == 1))) return rc;
     }
