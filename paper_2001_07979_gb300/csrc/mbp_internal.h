@@ -176,8 +176,16 @@ int stream_iterations(const DevCode& c, DevState& st, const DecodeArgs& a, bool 
 // one flooding iteration of one group, no host synchronisation (grouped decode; float arithmetic); iter = 1,
 // 2, 0 for a later iteration, or kStopTestOnly for the stopping test before iteration 1 alone
 constexpr int kStopTestOnly = -1;
+// Streams a step may fork onto while it is captured into a graph (independent launches then become parallel
+// branches): the variable-node classes of a pass after the first run on aux[0], aux[1], joined back to the
+// capturing stream through the events.
+struct StreamFork {
+  cudaStream_t aux[2];
+  cudaEvent_t fork, join[2];
+};
 template <typename M, typename S>
-cudaError_t stream_group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s);
+cudaError_t stream_group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s,
+                              const StreamFork* fork = nullptr);
 template <typename M>
 int resident_group(const DevCode& c, int n_tiles);
 template <typename M>

@@ -112,7 +112,7 @@ struct Groups {
 
 // ---- kernel launches of one batch, by message type
 struct Kernels {
-  cudaError_t (*group_step)(const DevCode&, const DevState&, int, double, cudaStream_t);
+  cudaError_t (*group_step)(const DevCode&, const DevState&, int, double, cudaStream_t, const StreamFork*);
   cudaError_t (*build_lists)(const MultiTables&, const MultiShape&, int, int, unsigned long long, const GroupConds&,
                              cudaStream_t);
   cudaError_t (*check)(const MultiTables&, const MultiShape&, int, const MultiTuning&, int, cudaStream_t);
@@ -145,7 +145,7 @@ cudaError_t issue_prologue(const Kernels& k, const MultiTables& tb, const MultiS
   if (tu.grid) {
     for (size_t g = 0; g < gs.code.size(); ++g) {
       if (gs.st[g].F == 0) continue;
-      if ((e = k.group_step(gs.code[g], gs.st[g], kStopTestOnly, gs.l_max, s)) != cudaSuccess) return e;
+      if ((e = k.group_step(gs.code[g], gs.st[g], kStopTestOnly, gs.l_max, s, nullptr)) != cudaSuccess) return e;
     }
     return k.build_lists(tb, sh, 2, in_graph, h, gc, s);
   }
@@ -164,7 +164,7 @@ cudaError_t issue_work(const Kernels& k, const MultiTables& tb, const MultiShape
   if (tu.grid) {
     for (size_t g = 0; g < gs.code.size(); ++g) {
       if (gs.st[g].F == 0) continue;
-      if ((e = k.group_step(gs.code[g], gs.st[g], iter, gs.l_max, s)) != cudaSuccess) return e;
+      if ((e = k.group_step(gs.code[g], gs.st[g], iter, gs.l_max, s, nullptr)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
@@ -194,7 +194,7 @@ cudaError_t issue_retire(const Kernels& k, const MultiTables& tb, const MultiSha
 // Grid kernels: one IF node per group with frames (parallel branches, each running its group's step while the
 // group has unfinished tiles), all depending on `deps`; returns the IF nodes.
 int add_group_branches(const Kernels& k, const Groups& gs, const GroupConds& gc, int iter, cudaGraph_t graph,
-                       const std::vector<cudaGraphNode_t>& deps, cudaStream_t cs,
+                       const std::vector<cudaGraphNode_t>& deps, cudaStream_t cs, const StreamFork* fork,
                        std::vector<cudaGraphNode_t>* nodes) {
   cudaError_t e;
   for (size_t g = 0; g < gs.code.size(); ++g) {
@@ -210,7 +210,7 @@ int add_group_branches(const Kernels& k, const Groups& gs, const GroupConds& gc,
     if ((e = cudaStreamBeginCaptureToGraph(cs, sub, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
         cudaSuccess)
       return cuda_error(e, "begin capture (group step)");
-    const cudaError_t ke = k.group_step(gs.code[g], gs.st[g], iter, gs.l_max, cs);
+    const cudaError_t ke = k.group_step(gs.code[g], gs.st[g], iter, gs.l_max, cs, fork);
     cudaGraph_t out = sub;
     const cudaError_t ee = cudaStreamEndCapture(cs, &out);
     if (ke != cudaSuccess) return cuda_error(ke, "group step during capture");
@@ -254,6 +254,7 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
   int rc = MBP_OK;
   GroupConds ga{0, {}}, g2{0, {}}, gb{0, {}};  // IF conditions of iterations 1, 2 and of the loop body
   std::vector<cudaGraphNode_t> leaf, branches;
+  StreamFork fork{};  // the variable-node classes of a group step as parallel branches
 #define GK(call, what)                 \
   if ((e = (call)) != cudaSuccess) {   \
     rc = cuda_error(e, what);          \
@@ -263,6 +264,11 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
   if ((rc = (call))) goto done;
   {
     GK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+    GK(cudaStreamCreateWithFlags(&fork.aux[0], cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+    GK(cudaStreamCreateWithFlags(&fork.aux[1], cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+    GK(cudaEventCreateWithFlags(&fork.fork, cudaEventDisableTiming), "cudaEventCreateWithFlags");
+    GK(cudaEventCreateWithFlags(&fork.join[0], cudaEventDisableTiming), "cudaEventCreateWithFlags");
+    GK(cudaEventCreateWithFlags(&fork.join[1], cudaEventDisableTiming), "cudaEventCreateWithFlags");
     GK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
     cudaGraphConditionalHandle h;
     GK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault), "cudaGraphConditionalHandleCreate");
@@ -284,11 +290,11 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
                      &leaf, "capture (prologue)"));
     if (tu.grid) {  // iterations 1 and 2
       branches.clear();
-      GR(add_group_branches(k, gs, ga, 1, g, leaf, cs, &branches));
+      GR(add_group_branches(k, gs, ga, 1, g, leaf, cs, &fork, &branches));
       GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, g2, st); },
                        &leaf, "capture (retire)"));
       branches.clear();
-      GR(add_group_branches(k, gs, g2, 2, g, leaf, cs, &branches));
+      GR(add_group_branches(k, gs, g2, 2, g, leaf, cs, &fork, &branches));
       GR(capture_after(g, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, gb, st); },
                        &leaf, "capture (retire)"));
     }
@@ -301,7 +307,7 @@ int build_graph(const Kernels& k, const MultiTables& tb, const MultiShape& sh, c
     cudaGraph_t body = p.conditional.phGraph_out[0];
     if (tu.grid) {
       branches.clear();
-      GR(add_group_branches(k, gs, gb, 0, body, {}, cs, &branches));
+      GR(add_group_branches(k, gs, gb, 0, body, {}, cs, &fork, &branches));
       GR(capture_after(body, branches, cs, [&](cudaStream_t st) { return issue_retire(k, tb, sh, tu, 1, h, gb, st); },
                        nullptr, "capture (loop body)"));
     } else {
@@ -319,6 +325,10 @@ done:
 #undef GK
   if (g) cudaGraphDestroy(g);
   if (cs) cudaStreamDestroy(cs);
+  for (cudaStream_t a : fork.aux)
+    if (a) cudaStreamDestroy(a);
+  for (cudaEvent_t ev : {fork.fork, fork.join[0], fork.join[1]})
+    if (ev) cudaEventDestroy(ev);
   return rc;
 }
 

@@ -398,9 +398,17 @@ inline bool rows_ok(const DevCode& c, const DevState& st) {
 // Eq. (2) for every node of every unfinished tile: one launch per degree class, or one over all nodes.
 // rows: iteration 1 in row form (rows_ok).
 template <typename M, typename S>
-void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) {
+void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s0, const StreamFork* fork = nullptr) {
   if (c.n_vclass > 0) {
+    // with a fork (graph capture), classes 1, 2, ... run on the auxiliary streams, beside class 0
+    const bool forked = fork && c.n_vclass > 1;
+    const int n_aux = forked ? (c.n_vclass - 1 < 2 ? c.n_vclass - 1 : 2) : 0;
+    if (forked) {
+      cudaEventRecord(fork->fork, s0);
+      for (int j = 0; j < n_aux; ++j) cudaStreamWaitEvent(fork->aux[j], fork->fork, 0);
+    }
     for (int k = 0; k < c.n_vclass; ++k) {
+      const cudaStream_t s = forked && k > 0 ? fork->aux[(k - 1) % 2] : s0;
       const int count = c.vclass_first[k + 1] - c.vclass_first[k], d = c.vclass_deg[k];
       if (rows) {  // classes of up to 32 edges (rows_ok), 32 / d nodes per warp
         const int per_warp = kLanes / d;
@@ -485,7 +493,13 @@ void launch_vn(const DevCode& c, const DevState& st, bool rows, cudaStream_t s) 
       else MBP_VN(64, 1);
 #undef MBP_VN
     }
+    if (forked)
+      for (int j = 0; j < n_aux; ++j) {
+        cudaEventRecord(fork->join[j], fork->aux[j]);
+        cudaStreamWaitEvent(s0, fork->join[j], 0);
+      }
   } else {
+    const cudaStream_t s = s0;
     vn_kernel<M, S><<<dim3(blocks_for(c.n, 8), st.n_tiles), 256, 0, s>>>(
         c, static_cast<const S*>(st.c2v), static_cast<M*>(st.lv), static_cast<const M*>(st.lp), st.yt,
         static_cast<const M*>(st.chan_mag), st.xh, st.active);
@@ -746,7 +760,8 @@ void launch_cn_any(const DevCode& c, const DevState& st, const CnLaunch& q, doub
 // iter: 1, 2, or 0 for any later iteration (iterations 1 and 2 differ in where their messages come from);
 // kStopTestOnly: the stopping test before iteration 1.
 template <typename M, typename S>
-cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s) {
+cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_max, cudaStream_t s,
+                       const StreamFork* fork = nullptr) {
   const bool rows = rows_ok(c, st);
   if (iter == kStopTestOnly) {  // with the row form, the sign words of iteration 1 and the test together
     if (rows) launch_first_rows_any(c, st, st.fail, s);
@@ -762,7 +777,7 @@ cudaError_t group_step(const DevCode& c, const DevState& st, int iter, double l_
   if (e != cudaSuccess) return e;
   prof_end(fam, s, q.rows == 1 ? 2 : 1);
   prof_begin(MBP_KERNEL_VARIABLE, s);
-  launch_vn<M, S>(c, st, rows && iter == 1, s);
+  launch_vn<M, S>(c, st, rows && iter == 1, s, fork);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   prof_end(MBP_KERNEL_VARIABLE, s, c.n_vclass > 0 ? c.n_vclass : 1);
   prof_begin(MBP_KERNEL_SYNDROME, s);

@@ -11,8 +11,8 @@ int stream_iterations<float, __nv_bfloat16>(const DevCode& c, DevState& st, cons
 
 template <>
 cudaError_t stream_group_step<float, __nv_bfloat16>(const DevCode& c, const DevState& st, int first_iter, double l_max,
-                                         cudaStream_t s) {
-  return stream::group_step<float, __nv_bfloat16>(c, st, first_iter, l_max, s);
+                                         cudaStream_t s, const StreamFork* fork) {
+  return stream::group_step<float, __nv_bfloat16>(c, st, first_iter, l_max, s, fork);
 }
 
 }  // namespace mbp

@@ -11,8 +11,8 @@ int stream_iterations<float, __half>(const DevCode& c, DevState& st, const Decod
 
 template <>
 cudaError_t stream_group_step<float, __half>(const DevCode& c, const DevState& st, int first_iter, double l_max,
-                                         cudaStream_t s) {
-  return stream::group_step<float, __half>(c, st, first_iter, l_max, s);
+                                         cudaStream_t s, const StreamFork* fork) {
+  return stream::group_step<float, __half>(c, st, first_iter, l_max, s, fork);
 }
 
 }  // namespace mbp

@@ -11,8 +11,8 @@ int stream_iterations<float, float>(const DevCode& c, DevState& st, const Decode
 
 template <>
 cudaError_t stream_group_step<float, float>(const DevCode& c, const DevState& st, int first_iter, double l_max,
-                                         cudaStream_t s) {
-  return stream::group_step<float, float>(c, st, first_iter, l_max, s);
+                                         cudaStream_t s, const StreamFork* fork) {
+  return stream::group_step<float, float>(c, st, first_iter, l_max, s, fork);
 }
 
 }  // namespace mbp
