@@ -199,19 +199,25 @@ __device__ __forceinline__ void cn_pair_row(int deg, const int* __restrict__ col
     v0[k] = on && h0 ? __ldg(g0 + col[k] * kLanes) : 0.f;
     v1[k] = on && h1 ? __ldg(g1 + col[k] * kLanes) : 0.f;
   }
-  if (rp) {  // lane k fetches edge k's sign words (two gathers for the row), broadcast per edge
+  if (rp) {
+    // lane k fetches edge k's sign words (two gathers for the row); one bit transpose per tile gives lane f
+    // every edge's bit of frame f (bit k: edge k). The old message of edge k is the row's magnitude with the
+    // sign bit lane of rs ^ y_k (row_msg); v - old is formed as v + (-old), which rounds the same, with -old's
+    // sign bit taken from bit k of ~(R) (R = the transposed word xor the row's own sign bit of this frame).
     const int lane = threadIdx.x & 31;
     const int mycol = lane < deg ? __ldg(cols + lane) : 0;
     const uint32_t my0 = lane < deg && h0 ? __ldg(rp->y0 + mycol) : 0u;
     const uint32_t my1 = lane < deg && h1 ? __ldg(rp->y1 + mycol) : 0u;
+    const uint32_t n0 = ~(warp_transpose32(my0) ^ (0u - ((rp->s0 >> lane) & 1u)));
+    const uint32_t n1 = ~(warp_transpose32(my1) ^ (0u - ((rp->s1 >> lane) & 1u)));
+    const uint32_t m0 = __float_as_uint(rp->m0) & ~kSign, m1 = __float_as_uint(rp->m1) & ~kSign;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const uint32_t y0k = __shfl_sync(kFull, my0, k & 31), y1k = __shfl_sync(kFull, my1, k & 31);
+    for (int k = 0; k < D; ++k)
       if (!CHECKED || k < deg) {
-        if (h0) v0[k] -= row_msg(rp->m0, rp->s0, y0k, lane);
-        if (h1) v1[k] -= row_msg(rp->m1, rp->s1, y1k, lane);
+        static_assert(D <= 32, "one transposed bit per edge");
+        if (h0) v0[k] += __uint_as_float(m0 | ((n0 << (31 - k)) & kSign));
+        if (h1) v1[k] += __uint_as_float(m1 | ((n1 << (31 - k)) & kSign));
       }
-    }
   } else if (!first_iter) {
 #pragma unroll
     for (int k = 0; k < D; ++k)
