@@ -270,16 +270,24 @@ __device__ __forceinline__ M row_msg(M rm, uint32_t rs, uint32_t y, int lane) {
 
 // 32 x 32 bit-matrix transpose across a warp: lane i holds row i (bit j =
 // A[i][j]); afterwards lane j holds column j (bit i = A[i][j]). Five exchange
-// rounds of block sizes 16, 8, 4, 2, 1, each swapping the off-diagonal blocks.
+// rounds of block sizes 16, 8, 4, 2, 1, each swapping the off-diagonal blocks:
+// a lane whose bit s is clear keeps the low halves of its 2s-bit blocks and
+// takes its partner's low halves into the high halves (partner word rotated
+// left by s), a lane whose bit s is set keeps the high halves and takes the
+// partner's high halves into the low halves (rotated right by s). One shuffle,
+// one funnel rotate and one bitwise select per round; the per-lane masks and
+// rotate amounts depend on the lane only.
 __device__ __forceinline__ uint32_t warp_transpose32(uint32_t a) {
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31;
   constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
-    const int s = 16 >> r;
-    const uint32_t m = kMask[r];
-    const uint32_t o = __shfl_xor_sync(kFull, a, s);
-    a = (lane & s) ? ((a & ~m) | ((o & ~m) >> s)) : ((a & m) | ((o & m) << s));
+    const uint32_t s = 16u >> r;
+    const uint32_t hi = uint32_t(int32_t(lane << (27 + r)) >> 31);  // all ones where lane bit s is set
+    const uint32_t keep = kMask[r] ^ hi;
+    const uint32_t amt = s ^ (hi & (s ^ (32u - s)));  // s, or 32 - s (a right rotation by s)
+    const uint32_t o = __shfl_xor_sync(kFull, a, int(s));
+    a = (a & keep) | (__funnelshift_l(o, o, amt) & ~keep);
   }
   return a;
 }
