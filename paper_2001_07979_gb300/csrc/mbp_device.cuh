@@ -751,7 +751,7 @@ __device__ __forceinline__ void syn_rows(const DevCode& c, int tile, int r0, uin
 __device__ __forceinline__ uint32_t update_tile(int tile, int F, int u, int t, int max_iter, int early_exit,
                                                 uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
                                                 int32_t* __restrict__ iters, uint8_t* __restrict__ success,
-                                                uint8_t* __restrict__ synd_ok) {
+                                                uint8_t* __restrict__ synd_ok, const int32_t* __restrict__ perm) {
   uint32_t act = __ldcg(active + tile);
   if (act == 0) return 0;
   uint32_t anyfail = 0;
@@ -759,14 +759,33 @@ __device__ __forceinline__ uint32_t update_tile(int tile, int F, int u, int t, i
   uint32_t done = 0;
   if (t >= max_iter) done = act;
   else if (early_exit) done = act & ~anyfail;
-  for (int lane = 0; lane < kLanes; ++lane) {
-    if (!((done >> lane) & 1u)) continue;
-    const int f = tile * kLanes + lane;
-    if (f >= F) continue;
-    iters[f] = t;
-    success[f] = uint8_t(!((anyfail >> lane) & 1u));
+  if (done) {
+    // the caller's frames of the tile's slots, loaded before any output is written
+    int fr[kLanes];
+    const int4* p4 = reinterpret_cast<const int4*>(perm + int64_t(tile) * kLanes);
+#pragma unroll
+    for (int k = 0; k < kLanes / 4; ++k) {
+      const int4 v = __ldg(p4 + k);
+      fr[4 * k] = v.x;
+      fr[4 * k + 1] = v.y;
+      fr[4 * k + 2] = v.z;
+      fr[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int lane = 0; lane < kLanes; ++lane) {
+      if (!((done >> lane) & 1u) || tile * kLanes + lane >= F) continue;
+      const int f = fr[lane];
+      iters[f] = t;
+      success[f] = uint8_t(!((anyfail >> lane) & 1u));
+    }
     if (synd_ok)
-      for (int l = 0; l < u; ++l) synd_ok[int64_t(f) * u + l] = uint8_t(!((__ldcg(fail + tile * u + l) >> lane) & 1u));
+      for (int l = 0; l < u; ++l) {
+        const uint32_t fw = __ldcg(fail + tile * u + l);
+#pragma unroll
+        for (int lane = 0; lane < kLanes; ++lane)
+          if (((done >> lane) & 1u) && tile * kLanes + lane < F)
+            synd_ok[int64_t(fr[lane]) * u + l] = uint8_t(!((fw >> lane) & 1u));
+      }
   }
   act &= ~done;
   active[tile] = act;

@@ -104,6 +104,11 @@ struct DevState {
   void* fmag;         // [n_tiles][kMaxRowDeg][kLanes] arithmetic type (rounded to the message type)
   uint32_t* rsgn;     // [m_tot][n_tiles] (row-major)
   uint32_t* ppos;     // [n_tiles] the lanes whose channel magnitude ln((1 - e)/e) is positive (BSC inputs)
+  // Frame order: the decoder's slot s = tile * kLanes + lane holds the caller's frame perm[s], and frame f sits
+  // in slot slot_of[f]. BSC inputs are ordered by QBER (ties by index), so that the frames of a tile need similar
+  // iteration counts and a tile retires close to when its frames do; LLR inputs keep their order.
+  int32_t* perm;      // [n_tiles * kLanes] (entries past F unused)
+  int32_t* slot_of;   // [n_tiles * kLanes]
   // staging for mbp_decode_bsc_host
   uint32_t* io_y;
   double* io_qber;

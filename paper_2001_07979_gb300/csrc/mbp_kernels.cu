@@ -77,18 +77,59 @@ __global__ void bsc_llr_kernel(const uint32_t* __restrict__ y, const double* __r
 // lanes past the last frame.
 template <typename M>
 __global__ void chan_mag_kernel(const double* __restrict__ qber, int F, int n_lanes, double unit,
-                                M* __restrict__ mag) {
+                                M* __restrict__ mag, const int32_t* __restrict__ perm) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n_lanes) return;
   M v = M(0);
   if (f < F) {
-    const double e = qber[f];
+    const double e = qber[perm[f]];
     v = M(log((1.0 - e) / e) * unit);
   }
   mag[f] = v;
 }
 
 // ------------------------------------------------------------- set-up
+
+// Batches up to this many frames are ordered by QBER (the rank of every frame is
+// counted over all frames: F^2 comparisons, under a millisecond at this size);
+// larger ones keep the caller's order.
+constexpr int kOrderMax = 1 << 16;
+
+// The frame held by each slot (perm) and the slot of each frame (slot_of). With
+// per-frame QBERs, slots follow ascending QBER, ties in frame order (a stable
+// order over the doubles' bit patterns mapped to a total order, so that every
+// input gives a permutation); otherwise, and for F > kOrderMax, slot = frame.
+// Slots past F hold themselves. One warp per slot index f: the lanes compare
+// frame f's key with every 32nd frame's and the ballots' population counts add
+// up to f's rank.
+__global__ void __launch_bounds__(256) frame_order_kernel(const double* __restrict__ qber, int F, int n_slots,
+                                                          int32_t* __restrict__ perm, int32_t* __restrict__ slot_of) {
+  const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (f >= n_slots) return;
+  if (f >= F || qber == nullptr || F > kOrderMax) {
+    if (lane == 0) {
+      perm[f] = f;
+      if (f < F) slot_of[f] = f;
+    }
+    return;
+  }
+  auto key = [](double q) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(q));
+    return (b >> 63) ? ~b : (b | (1ull << 63));
+  };
+  const unsigned long long kf = key(__ldg(qber + f));
+  int rank = 0;
+  for (int g0 = 0; g0 < F; g0 += kLanes) {
+    const int g = g0 + lane;
+    const unsigned long long kg = g < F ? key(__ldg(qber + g)) : ~0ull;
+    rank += __popc(__ballot_sync(kFull, g < F && (kg < kf || (kg == kf && g < f))));
+  }
+  if (lane == 0) {
+    perm[rank] = f;
+    slot_of[f] = rank;
+  }
+}
 
 // BSC inputs: Bob's bits into one word per (tile, node) with bit = lane (the
 // sign words of L_P = (1 - 2y) mag, eq. 5), and the hard decision of iteration
@@ -97,14 +138,15 @@ __global__ void chan_mag_kernel(const double* __restrict__ qber, int F, int n_la
 // word.
 template <typename M>
 __global__ void init_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ y, const M* __restrict__ mag,
-                                 uint32_t* __restrict__ yt, uint32_t* __restrict__ xh, uint32_t* __restrict__ ppos) {
+                                 uint32_t* __restrict__ yt, uint32_t* __restrict__ xh, uint32_t* __restrict__ ppos,
+                                 const int32_t* __restrict__ perm) {
   const int wn = (c.n + 31) >> 5;
   const int tile = blockIdx.y;
   const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (w >= wn) return;
   const int lane = threadIdx.x & 31;
   const int f = tile * kLanes + lane;
-  const uint32_t yw = f < F ? y[int64_t(f) * wn + w] : 0u;
+  const uint32_t yw = f < F ? y[int64_t(perm[f]) * wn + w] : 0u;
   const uint32_t pos = __ballot_sync(kFull, mag[tile * kLanes + lane] > M(0));
   if (w == 0 && lane == 0) ppos[tile] = pos;
   const uint32_t word = warp_transpose32(yw);  // lane b: node 32 w + b, bit = frame
@@ -141,7 +183,7 @@ __global__ void init_lp_kernel(const DevCode c, int F, const M* __restrict__ llr
 // word of one matrix): lane f reads frame f's word, and a warp bit transpose
 // gives lane b the word of row 32 g + b of H_l.
 __global__ void init_z_kernel(const DevCode c, int F, int n_tiles, const uint32_t* __restrict__ z,
-                              uint32_t* __restrict__ zt, uint32_t* __restrict__ ztt) {
+                              uint32_t* __restrict__ zt, uint32_t* __restrict__ ztt, const int32_t* __restrict__ perm) {
   const int tile = blockIdx.y;
   int g = blockIdx.x * 8 + (threadIdx.x >> 5);  // word over all matrices, then within H_l
   int l = 0;
@@ -156,7 +198,7 @@ __global__ void init_z_kernel(const DevCode c, int F, int n_tiles, const uint32_
   const int wl = (c.m[l] + 31) >> 5;
   const int lane = threadIdx.x & 31;
   const int f = tile * kLanes + lane;
-  const uint32_t word = warp_transpose32(f < F ? z[off + int64_t(f) * wl + g] : 0u);
+  const uint32_t word = warp_transpose32(f < F ? z[off + int64_t(perm[f]) * wl + g] : 0u);
   const int j = g * 32 + lane;
   if (j < c.m[l]) {
     const int p = c.row_at[c.row_first[l] + j];
@@ -178,7 +220,8 @@ __global__ void init_tiles_kernel(int F, int n_tiles, int u, uint32_t* __restric
 
 // One warp per (tile, 32-node word): lane i reads node 32 w + i's decision word
 // (one bit per frame); a warp bit transpose gives lane f frame f's output word.
-__global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ xh, uint32_t* __restrict__ out) {
+__global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restrict__ xh, uint32_t* __restrict__ out,
+                                const int32_t* __restrict__ perm) {
   const int wn = (c.n + 31) >> 5;
   const int tile = blockIdx.y;
   const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -188,17 +231,19 @@ __global__ void out_bits_kernel(const DevCode c, int F, const uint32_t* __restri
   const uint32_t word = i < c.n ? xh[int64_t(i) * gridDim.y + tile] : 0u;
   const uint32_t bits = warp_transpose32(word);  // lane f: frame f's bits of nodes 32 w .. 32 w + 31
   const int f = tile * kLanes + lane;
-  if (f < F) out[int64_t(f) * wn + w] = bits;
+  if (f < F) out[int64_t(perm[f]) * wn + w] = bits;
 }
 
 template <typename M>
 __global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv, const M* __restrict__ lp,
                                 const uint32_t* __restrict__ yt, const M* __restrict__ ymag,
-                                const int32_t* __restrict__ iters, M* __restrict__ out) {
+                                const int32_t* __restrict__ iters, M* __restrict__ out,
+                                const int32_t* __restrict__ slot_of) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= int64_t(F) * c.n) return;
-  const int f = int(idx / c.n), i = int(idx % c.n);
-  const int tile = f / kLanes, lane = f % kLanes;
+  const int f = int(idx / c.n), i = int(idx % c.n);  // the caller's frame f, at slot slot_of[f]
+  const int sl = slot_of[f];
+  const int tile = sl / kLanes, lane = sl % kLanes;
   const int64_t tn = int64_t(tile) * c.n + i;
   const M v = iters[f] == 0 ? channel_llr<M, kPolStream>(lp, yt, ymag, tn, tile, lane) : lv[tn * kLanes + lane];
   out[idx] = M(v * Arith<M>::kToLLR);
@@ -209,10 +254,12 @@ __global__ void soft_out_kernel(const DevCode c, int F, const M* __restrict__ lv
 template <typename M, typename S>
 __global__ void export_c2v_kernel(const DevCode c, const S* __restrict__ c2v, int frame, M* __restrict__ out,
                                   int n_tiles, const M* __restrict__ fmag, const uint32_t* __restrict__ rsgn,
-                                  const uint32_t* __restrict__ yt, const int32_t* __restrict__ counters) {
+                                  const uint32_t* __restrict__ yt, const int32_t* __restrict__ counters,
+                                  const int32_t* __restrict__ slot_of) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= c.e_tot) return;
-  const int tile = frame / kLanes, lane = frame % kLanes;
+  const int sl = slot_of[frame];
+  const int tile = sl / kLanes, lane = sl % kLanes;
   const int slot = c.edge_slot[e];
   M v;
   if (counters[2]) {
@@ -244,12 +291,15 @@ int setup_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s)
   const int F = st.F, NT = st.n_tiles;
   CK(cudaMemsetAsync(st.counters, 0, 4 * sizeof(int32_t), s), "clear counters");
   prof_begin(MBP_KERNEL_SETUP, s);
+  frame_order_kernel<<<blocks_for(NT * kLanes, 8), 256, 0, s>>>(a.y_bits ? a.qber : nullptr, F, NT * kLanes,
+                                                                st.perm, st.slot_of);
+  CKL("frame_order_kernel");
   if (a.y_bits) {  // BSC inputs: sign words and per-frame magnitudes, no LLR array
     chan_mag_kernel<M><<<blocks_for(NT * kLanes, 256), 256, 0, s>>>(a.qber, F, NT * kLanes, Arith<M>::kToInternal,
-                                                                   static_cast<M*>(st.chan_mag));
+                                                                   static_cast<M*>(st.chan_mag), st.perm);
     CKL("chan_mag_kernel");
     init_bits_kernel<M><<<dim3(blocks_for((c.n + 31) >> 5, 8), NT), 256, 0, s>>>(
-        c, F, a.y_bits, static_cast<const M*>(st.chan_mag), st.yt, st.xh, st.ppos);
+        c, F, a.y_bits, static_cast<const M*>(st.chan_mag), st.yt, st.xh, st.ppos, st.perm);
     CKL("init_bits_kernel");
   } else {
     st.yt = nullptr;
@@ -261,11 +311,11 @@ int setup_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s)
   int zwords = 0;
   for (int l = 0; l < c.u; ++l) zwords += (c.m[l] + 31) >> 5;
   if (zwords > 0)
-    init_z_kernel<<<dim3(blocks_for(zwords, 8), NT), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt, st.ztt);
+    init_z_kernel<<<dim3(blocks_for(zwords, 8), NT), 256, 0, s>>>(c, F, NT, a.z_bits, st.zt, st.ztt, st.perm);
   CKL("init_z_kernel");
   init_tiles_kernel<<<blocks_for(NT, 256), 256, 0, s>>>(F, NT, c.u, st.active, st.fail);
   CKL("init_tiles_kernel");
-  prof_end(MBP_KERNEL_SETUP, s, a.y_bits ? 4 : 3);
+  prof_end(MBP_KERNEL_SETUP, s, a.y_bits ? 5 : 4);
   if (a.validate) {
     int32_t host_ctr[4];
     CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof host_ctr, cudaMemcpyDeviceToHost, s), "read validate flag");
@@ -282,12 +332,12 @@ int output_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
   const int F = st.F, NT = st.n_tiles;
   const int wn = (c.n + 31) >> 5;
   prof_begin(MBP_KERNEL_OUTPUT, s);
-  out_bits_kernel<<<dim3(blocks_for(wn, 8), NT), 256, 0, s>>>(c, F, st.xh, a.x_hat_bits);
+  out_bits_kernel<<<dim3(blocks_for(wn, 8), NT), 256, 0, s>>>(c, F, st.xh, a.x_hat_bits, st.perm);
   CKL("out_bits_kernel");
   if (a.soft_out) {
     soft_out_kernel<M><<<blocks_for(int64_t(F) * c.n, 256), 256, 0, s>>>(
         c, F, static_cast<const M*>(st.lv), static_cast<const M*>(st.lp), st.yt, static_cast<const M*>(st.chan_mag),
-        a.iters, static_cast<M*>(a.soft_out));
+        a.iters, static_cast<M*>(a.soft_out), st.slot_of);
     CKL("soft_out_kernel");
   }
   prof_end(MBP_KERNEL_OUTPUT, s, a.soft_out ? 2 : 1);
@@ -339,7 +389,7 @@ int decode_t(const DevCode& c, DevState& st, const DecodeArgs& a, cudaStream_t s
 #undef CK
 }
 
-constexpr int kRegions = 22;
+constexpr int kRegions = 23;
 
 // bytes of one stored message and of one posterior / channel value
 size_t msg_size(int msg_dtype) {
@@ -378,6 +428,7 @@ void layout(const DevCode& c, int F, int msg_dtype, bool host_io, size_t* offs, 
       NT * size_t(c.m_tot) * 4,                                       // rsgn
       NT * size_t(c.m_tot) * 4,                                       // ztt
       NT * 4,                                                         // ppos
+      2 * NT * kLanes * 4,                                            // perm, slot_of
   };
   size_t t = 0;
   for (int i = 0; i < kRegions; ++i) {
@@ -436,6 +487,8 @@ void carve_workspace(const DevCode& c, int F, int msg_dtype, bool host_io, void*
   st->rsgn = reinterpret_cast<uint32_t*>(b + o[19]);
   st->ztt = reinterpret_cast<uint32_t*>(b + o[20]);
   st->ppos = reinterpret_cast<uint32_t*>(b + o[21]);
+  st->perm = reinterpret_cast<int32_t*>(b + o[22]);
+  st->slot_of = st->perm + int64_t(st->n_tiles) * kLanes;
   st->counters = reinterpret_cast<int32_t*>(b + o[9]);
   st->ctl = b + o[10];
   st->io_y = host_io ? reinterpret_cast<uint32_t*>(b + o[11]) : nullptr;
@@ -493,7 +546,8 @@ cudaError_t launch_export_c2v(const DevCode& c, const DevState& st, int msg_dtyp
   const unsigned grid = blocks_for(c.e_tot, 256);
 #define MBP_EXPORT(M, S)                                                                                     \
   export_c2v_kernel<M, S><<<grid, 256, 0, s>>>(c, static_cast<const S*>(st.c2v), frame, static_cast<M*>(out), \
-                                               st.n_tiles, static_cast<const M*>(st.fmag), st.rsgn, st.yt, st.counters)
+                                               st.n_tiles, static_cast<const M*>(st.fmag), st.rsgn, st.yt, st.counters, \
+                                               st.slot_of)
   if (msg_dtype == MBP_MSG_F64) MBP_EXPORT(double, double);
   else if (msg_dtype == MBP_MSG_F16) MBP_EXPORT(float, __half);
   else if (msg_dtype == MBP_MSG_BF16) MBP_EXPORT(float, __nv_bfloat16);

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(1024) lists_kernel(MultiGroup* __restrict__ gr
       MultiGroup& G = gr[tile_group[gt]];
       const int tile = gt - G.tile_base;
       act = retire ? update_tile(tile, G.st.F, G.c.u, t, max_iter, early, G.st.active, G.st.fail, G.iters,
-                                 G.success, G.synd_ok)
+                                 G.success, G.synd_ok, G.st.perm)
                    : G.st.active[tile];
       if (act) {
         if (gc.n) g_active[tile_group[gt]] = 1;

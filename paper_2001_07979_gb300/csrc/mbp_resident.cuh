@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
                                                        uint32_t* __restrict__ xh, const uint32_t* __restrict__ zt,
                                                        uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
                                                        int32_t* __restrict__ iters, uint8_t* __restrict__ success,
-                                                       uint8_t* __restrict__ synd_ok, ResidentCtl* ctl,
+                                                       uint8_t* __restrict__ synd_ok,
+                                                       const int32_t* __restrict__ perm, ResidentCtl* ctl,
                                                        BarrierCfg bc) {
   unsigned gen = 0;
   const int warps = gridDim.x * (blockDim.x >> 5);
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) resident_kernel(const DevCode c, int F, i
       __threadfence();
       int any = 0;
       for (int i = threadIdx.x; i < gt; i += blockDim.x)
-        any |= update_tile(g0 + i, F, c.u, t, max_iter, early_exit, active, fail, iters, success, synd_ok) != 0;
+        any |= update_tile(g0 + i, F, c.u, t, max_iter, early_exit, active, fail, iters, success, synd_ok, perm) != 0;
       any = __syncthreads_or(any);
       if (threadIdx.x == 0) {
         ctl->any_active = any;
@@ -163,6 +164,7 @@ cudaError_t launch_resident(const DevCode& c, const DevState& st, const DecodeAr
   int32_t* iters = a.iters;
   uint8_t* success = a.success;
   uint8_t* synd_ok = a.synd_ok;
+  const int32_t* perm = st.perm;
   ResidentCtl* ctl = static_cast<ResidentCtl*>(st.ctl);
   DevCode cc = c;
   const unsigned grid = unsigned(per_sm * sms);
@@ -172,7 +174,7 @@ cudaError_t launch_resident(const DevCode& c, const DevState& st, const DecodeAr
   if (const char* ev = std::getenv("MBP_TEST_BARRIER_EXTRA_ARRIVALS")) bc.arrivals += unsigned(std::atoi(ev));
   if (const char* ev = std::getenv("MBP_TEST_BARRIER_TIMEOUT_US")) bc.timeout = std::atoll(ev) * 2000LL;
   void* args[] = {&cc, &F, &NT, &G, &max_iter, &early_exit, &lm, &c2v, &lv, &lp, &yt, &ymag, &xh, &zt, &active, &fail,
-                  &iters, &success, &synd_ok, &ctl, &bc};
+                  &iters, &success, &synd_ok, &perm, &ctl, &bc};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(256), args, 0, s);
 }
 

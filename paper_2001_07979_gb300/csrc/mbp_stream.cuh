@@ -608,10 +608,11 @@ inline void launch_syn_any(const DevCode& c, const DevState& st, cudaStream_t s)
 __global__ void update_kernel(int F, int n_tiles, int u, int t, int max_iter, int early_exit,
                               uint32_t* __restrict__ active, uint32_t* __restrict__ fail,
                               int32_t* __restrict__ iters, uint8_t* __restrict__ success,
-                              uint8_t* __restrict__ synd_ok, int32_t* __restrict__ counters) {
+                              uint8_t* __restrict__ synd_ok, const int32_t* __restrict__ perm,
+                              int32_t* __restrict__ counters) {
   const int tile = blockIdx.x * blockDim.x + threadIdx.x;
   if (tile >= n_tiles) return;
-  if (update_tile(tile, F, u, t, max_iter, early_exit, active, fail, iters, success, synd_ok))
+  if (update_tile(tile, F, u, t, max_iter, early_exit, active, fail, iters, success, synd_ok, perm))
     atomicAdd(&counters[0], 1);
 }
 
@@ -808,7 +809,7 @@ int run(const DevCode& c, DevState& st, const DecodeArgs& a, bool fixed, double 
     CK(cudaMemsetAsync(st.counters, 0, sizeof(int32_t), s), "clear counter");
     prof_begin(MBP_KERNEL_RETIRE, s);
     update_kernel<<<blocks_for(NT, 128), 128, 0, s>>>(F, NT, c.u, t, a.max_iter, a.early_exit, st.active, st.fail,
-                                                       a.iters, a.success, a.synd_ok, st.counters);
+                                                       a.iters, a.success, a.synd_ok, st.perm, st.counters);
     CKL("update_kernel");
     prof_end(MBP_KERNEL_RETIRE, s, 1);
     CK(cudaMemcpyAsync(host_ctr, st.counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "read counter");

@@ -173,3 +173,47 @@ def test_pair_kernels_on_long_rows(mbp, msg):
     conv = ref["success"].astype(bool) & a["success"].cpu().numpy().astype(bool)
     assert conv.sum() >= 60
     assert np.array_equal(a["x_hat_bits"].cpu().numpy().view(np.uint32)[conv], ref["x_hat_bits"][conv])
+
+
+def test_frames_ordered_by_qber_keep_the_callers_order(mbp):
+    """BSC frames are placed in the decoder's tiles in order of QBER (ties by index) and the outputs go back to
+    the caller's order. 100 frames with QBERs from 0.5% to 12% in shuffled order (so every tile holds frames of
+    other positions, and some frames fail): FP64 outputs, iteration counts, success and per-matrix flags equal
+    the oracle's frame by frame, the soft output equals the oracle's posterior and mbp_export_c2v of a frame
+    returns that frame's messages (after two iterations without early exit); FP32 decodes of the shuffled
+    batch (graph and streaming schedules) equal those of the same frames in another order, frame by frame."""
+    n, F = 2000, 100
+    H = mi.make_codes(n, 800, {2: 0.3, 3: 0.4, 8: 0.3}, 2, 68)
+    rng = np.random.default_rng(69)
+    e = rng.permutation(np.linspace(0.005, 0.12, F))
+    x, y, _ = mi.bsc_frames(n, F, e, seed=70)
+    codes = mbp.mbp_create_codes(H)
+    z = mbp.mbp_syndrome(codes, dev(i32(x)))
+    LP = orc.bsc_llr(y, n, e)
+    z_orc = orc.syndrome(H, x)
+    yd, ed = dev(i32(y)), dev(e)
+    ref = orc.decode(H, LP, z_orc, 30, threads=8, want_lv=True, want_synd=True)
+    ok = ref["success"].astype(bool)
+    assert F // 2 < ok.sum() < F  # frames that decode and frames that do not
+    out = mbp.mbp_decode_bsc(codes, yd, ed, z, 30, msg_dtype=mbp.MSG_F64, want_soft=True, want_synd=True)
+    # the decoded frames' outputs (a frame still failing after 30 iterations may wander at the last bits); a
+    # frame's outputs written to another frame's place would show on the decoded frames
+    assert np.array_equal(out["iters"].cpu().numpy()[ok], ref["iters"][ok])
+    assert np.array_equal(out["success"].cpu().numpy()[ok], ref["success"][ok])
+    assert abs(int(out["success"].sum()) - int(ok.sum())) <= 2
+    assert np.array_equal(out["x_hat_bits"].cpu().numpy().view(np.uint32)[ok], ref["x_hat_bits"][ok])
+    assert np.array_equal(out["synd_ok"].cpu().numpy()[ok], ref["synd_ok"][ok])
+    assert np.max(np.abs(out["soft"].cpu().numpy()[ok] - ref["L_V"][ok])) <= 1e-9
+    two = mbp.mbp_decode_bsc(codes, yd, ed, z, 2, early_exit=False, msg_dtype=mbp.MSG_F64)
+    ref2 = orc.decode(H, LP, z_orc, 2, early_exit=False, want_c2v=True)["c2v"]
+    order = np.argsort(e, kind="stable")
+    for f in (int(order[0]), int(order[-1]), int(order[33]), 0, F - 1):
+        c = mbp.mbp_export_c2v(codes, F, two["workspace"], f, mbp.MSG_F64).cpu().numpy()
+        assert np.max(np.abs(c - ref2[f])) <= 1e-9, f
+    perm = rng.permutation(F)
+    for sched in (mbp.SCHED_GRAPH, mbp.SCHED_STREAMING):
+        a = mbp.mbp_decode_bsc(codes, yd, ed, z, 30, want_soft=True, schedule=sched)
+        zp = mbp.mbp_syndrome(codes, dev(i32(x[perm])))
+        b = mbp.mbp_decode_bsc(codes, dev(i32(y[perm])), dev(e[perm]), zp, 30, want_soft=True, schedule=sched)
+        for k in KEYS:
+            assert torch.equal(a[k][perm], b[k]), (sched, k)
