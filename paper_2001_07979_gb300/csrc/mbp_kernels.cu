@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(256) frame_order_kernel(const double* __restri
   };
   const unsigned long long kf = key(__ldg(qber + f));
   int rank = 0;
-  for (int g0 = 0; g0 < F; g0 += kLanes) {
+#pragma unroll 8
+  for (int g0 = 0; g0 < F; g0 += kLanes) {  // unrolled: several key loads in flight
     const int g = g0 + lane;
     const unsigned long long kg = g < F ? key(__ldg(qber + g)) : ~0ull;
     rank += __popc(__ballot_sync(kFull, g < F && (kg < kf || (kg == kf && g < f))));
