@@ -696,9 +696,11 @@ def run_uneven(args):
                             "f": sp["m"] / (sp["n"] * h(q)), "f_leak": sp["u"] * sp["m"] / (sp["n"] * h(q))})
         if sp["frames"]:
             # work in edge x frame x iteration units: per frame as run, and as a tile pair (64 frames) costs,
-            # since the kernels move a pair's messages until its last frame has stopped
+            # since the kernels move a pair's messages until its last frame has stopped; the decoder places a
+            # group's frames in its tiles in order of QBER (ties by index), so the pairs are formed that way
             e_tot = g["codes"].edges
-            pair_max = [int(it[q:q + 64].max()) for q in range(0, it.size, 64)]
+            its = it[np.argsort(sp["qber"], kind="stable")]
+            pair_max = [int(its[q:q + 64].max()) for q in range(0, its.size, 64)]
             per_group.append({"n": sp["n"], "rate": sp["rate"], "u": sp["u"], "frames": sp["frames"],
                               "mean_iterations": float(it.mean()), "max_iterations": int(it.max()),
                               "edge_frame_iterations": int(e_tot) * int(it.sum()),
