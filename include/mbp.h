@@ -240,6 +240,11 @@ int mbp_decode_batch(const mbp_codes* codes, int F, const void* llr, const uint3
 /*
  * mbp_decode_batch for BSC frames with the channel LLR of eq. (5) formed on the
  * device from Bob's bits: y_bits device [F][ceil(n/32)], qber device [F].
+ * The decoder places the frames in its tiles of 32 in order of QBER (ties in
+ * frame order; batches of up to 65,536 frames), so that the frames of a tile
+ * need similar numbers of iterations and a tile stops close to when its frames
+ * do. A frame's results do not depend on the other frames of the batch or on
+ * their order, and every output is in the caller's frame order.
  */
 int mbp_decode_bsc(const mbp_codes* codes, int F, const uint32_t* y_bits, const double* qber,
                    const uint32_t* z_bits, int max_iter, const mbp_opts* opts, uint32_t* x_hat_bits,
